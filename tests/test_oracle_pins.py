@@ -1,0 +1,311 @@
+"""Pins of the FP64 CPU oracle against things other than itself.
+
+Each test checks an oracle routine against the mathematics: the dense
+matricized definition, a library sparse product, closed forms, exact integer
+arithmetic, invariants, brute force on tiny inputs, or recovery of a known
+CP model.  None of them re-types the oracle's own loop.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def _dense(idx, vals, dims):
+    X = np.zeros(dims)
+    np.add.at(X, tuple(idx.astype(np.int64)), vals.astype(np.float64))
+    return X
+
+
+def _khatri_rao_unfold_mttkrp(X, factors, n, R):
+    """V = X_(n) (A^(d) (.) ... (.) A^(n+1) (.) A^(n-1) (.) ... (.) A^(1)), the
+    matricized form of MTTKRP (Kolda-Bader ordering: lower modes vary fastest)."""
+    d = X.ndim
+    In = X.shape[n]
+    Xn = np.moveaxis(X, n, 0).reshape(In, -1, order="F")
+    others = [m for m in range(d) if m != n]
+    KR = np.empty((Xn.shape[1], R))
+    for j in range(R):
+        col = np.ones(1)
+        for m in others:  # kron(a_m, col): the new (higher) mode varies slowest
+            col = np.kron(factors[m][:, j], col)
+        KR[:, j] = col
+    return Xn @ KR
+
+
+@pytest.mark.parametrize("dims,nnz,R,seed", [
+    ((7, 5, 6), 60, 4, 1),
+    ((4, 6, 3, 5), 80, 3, 2),
+    ((3, 4, 2, 3, 2), 40, 5, 3),
+])
+def test_mttkrp_matches_dense_unfolding(dims, nnz, R, seed):
+    idx, vals = synth.coo_uniform(dims, nnz, seed)  # duplicates allowed (additive)
+    facs = [f[:, :R].astype(np.float64) for f in synth.factor_matrices(dims, R, seed, "normal")]
+    lam = np.random.default_rng(seed).uniform(0.5, 2.0, R)
+    X = _dense(idx, vals, dims)
+    for n in range(len(dims)):
+        ref = _khatri_rao_unfold_mttkrp(X, facs, n, R) * lam[None, :]
+        got = oracle.mttkrp(idx, vals, dims, facs, n, R, lam=lam)
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_mttkrp_order2_is_spmm():
+    import scipy.sparse as sp
+    dims = (40, 30)
+    idx, vals = synth.coo_uniform(dims, 300, 5)
+    R = 6
+    facs = [f[:, :R].astype(np.float64) for f in synth.factor_matrices(dims, R, 5, "normal")]
+    X = sp.coo_matrix((vals.astype(np.float64), (idx[0], idx[1])), shape=dims).tocsr()
+    np.testing.assert_allclose(oracle.mttkrp(idx, vals, dims, facs, 0, R), X @ facs[1],
+                               rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(oracle.mttkrp(idx, vals, dims, facs, 1, R), X.T @ facs[0],
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_single_nonzero_closed_form():
+    dims = (5, 4, 3)
+    idx = np.array([[3], [1], [2]], dtype=np.int32)
+    vals = np.array([2.5], dtype=np.float32)
+    R = 3
+    facs = [np.arange(I * R, dtype=np.float64).reshape(I, R) + 1 for I in dims]
+    for n in range(3):
+        V = oracle.mttkrp(idx, vals, dims, facs, n, R)
+        expect = np.zeros((dims[n], R))
+        row = 2.5 * np.ones(R)
+        for m in range(3):
+            if m != n:
+                row = row * facs[m][idx[m, 0]]
+        expect[idx[n, 0]] = row
+        np.testing.assert_array_equal(V, expect)
+
+
+def test_all_ones_factors_give_slice_sums():
+    dims = (20, 15, 10)
+    idx, vals = synth.coo_uniform(dims, 500, 9)
+    R = 4
+    facs = [np.ones((I, R)) for I in dims]
+    for n in range(3):
+        V = oracle.mttkrp(idx, vals, dims, facs, n, R)
+        sums = np.bincount(idx[n], weights=vals.astype(np.float64), minlength=dims[n])
+        np.testing.assert_allclose(V, np.repeat(sums[:, None], R, axis=1), rtol=1e-13)
+
+
+def test_integer_case_is_exact():
+    dims = (30, 20, 10, 7)
+    idx, vals, facs = synth.small_integer_case(dims, 2000, 5, 11)
+    R = 5
+    F = [f[:, :R].astype(np.int64) for f in facs]
+    for n in range(4):
+        prod = vals.astype(np.int64)[:, None] * np.ones((1, R), dtype=np.int64)
+        for m in range(4):
+            if m != n:
+                prod = prod * F[m][idx[m]]
+        exact = np.zeros((dims[n], R), dtype=np.int64)
+        np.add.at(exact, idx[n], prod)
+        got = oracle.mttkrp(idx, vals, dims, [f.astype(np.float64) for f in F], n, R)
+        np.testing.assert_array_equal(got, exact.astype(np.float64))
+
+
+def test_linearity_and_order_invariance():
+    dims = (12, 9, 8)
+    R = 4
+    i1, v1 = synth.coo_uniform(dims, 200, 21)
+    i2, v2 = synth.coo_uniform(dims, 150, 22)
+    facs = [f[:, :R].astype(np.float64) for f in synth.factor_matrices(dims, R, 21, "normal")]
+    a, b = 0.75, -2.0  # exact in binary, so the scaled values are exact
+    idx = np.concatenate([i1, i2], axis=1)
+    vals = np.concatenate([a * v1.astype(np.float64), b * v2.astype(np.float64)])
+    perm = np.random.default_rng(0).permutation(idx.shape[1])
+    for n in range(3):
+        lhs = oracle.mttkrp(idx, vals, dims, facs, n, R)
+        rhs = a * oracle.mttkrp(i1, v1, dims, facs, n, R) + b * oracle.mttkrp(i2, v2, dims, facs, n, R)
+        np.testing.assert_allclose(lhs, rhs, rtol=1e-12, atol=1e-12)
+        shuf = oracle.mttkrp(idx[:, perm], vals[perm], dims, facs, n, R)
+        np.testing.assert_allclose(shuf, lhs, rtol=1e-12, atol=1e-12)
+
+
+def test_mttkrp_rows_matches_full():
+    dims = (50, 40, 30)
+    R = 6
+    idx, vals = synth.coo_zipf(dims, 3000, 1.1, 4)
+    facs = [f[:, :R].astype(np.float64) for f in synth.factor_matrices(dims, R, 4, "normal")]
+    lam = np.linspace(0.5, 1.5, R)
+    rows = np.array([0, 7, 7, 49, 13], dtype=np.int32)
+    for n in range(3):
+        full = oracle.mttkrp(idx, vals, dims, facs, n, R, lam=lam)
+        r = rows[rows < dims[n]]
+        np.testing.assert_array_equal(oracle.mttkrp_rows(idx, vals, dims, facs, n, R, r, lam=lam),
+                                      full[r])
+
+
+def test_stable_argsort_brute_force():
+    rng = np.random.default_rng(3)
+    for P, K in [(0, 3), (1, 1), (50, 3), (500, 40), (2000, 2000)]:
+        keys = rng.integers(0, K, size=P).astype(np.int32)
+        ref = sorted(range(P), key=lambda i: (int(keys[i]), i))
+        np.testing.assert_array_equal(oracle.stable_argsort(keys), np.array(ref, dtype=np.int32))
+        np.testing.assert_array_equal(oracle.stable_argsort(keys), np.argsort(keys, kind="stable"))
+
+
+def test_coalesce_brute_force():
+    dims = (6, 5, 4)
+    idx, vals = synth.coo_zipf(dims, 400, 1.5, 8)
+    acc = {}
+    for i in range(idx.shape[1]):
+        key = tuple(int(x) for x in idx[:, i])
+        acc[key] = acc.get(key, 0.0) + float(vals[i])
+    keys = sorted(acc)
+    ci, cv = oracle.coalesce(idx, vals)
+    assert ci.shape[1] == len(keys)
+    np.testing.assert_array_equal(ci.T, np.array(keys, dtype=np.int32))
+    np.testing.assert_allclose(cv, [acc[k] for k in keys], rtol=1e-15)
+    X = _dense(idx, vals, dims)
+    assert abs(oracle.norm2(idx, vals) - float((X * X).sum())) < 1e-12 * float((X * X).sum())
+
+
+def test_gram_and_cholesky():
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((200, 12))
+    G = oracle.gram(A)
+    np.testing.assert_allclose(G, A.T @ A, rtol=1e-12, atol=1e-12)
+    L = oracle.cholesky(G)
+    assert np.allclose(np.triu(L, 1), 0.0)
+    assert np.linalg.norm(L @ L.T - G) <= 1e-13 * np.linalg.norm(G)
+    np.testing.assert_allclose(L, np.linalg.cholesky(G), rtol=1e-10, atol=1e-12)
+    # not positive definite -> None
+    B = rng.standard_normal((5, 8))
+    assert oracle.cholesky(B.T @ B) is None
+    assert oracle.cholesky(-np.eye(3)) is None
+
+
+def _sparse_ktensor(dims, R, seed, density=0.35):
+    """Rank-R model whose factors have sparse support, densified to COO."""
+    rng = np.random.default_rng(seed)
+    facs = []
+    for I in dims:
+        A = rng.uniform(0.5, 1.5, (I, R)) * (rng.random((I, R)) < density)
+        for j in range(R):  # every column has support
+            if not A[:, j].any():
+                A[rng.integers(I), j] = 1.0
+        facs.append(A)
+    X = np.einsum("ir,jr,kr->ijk", *facs)
+    nz = np.nonzero(X)
+    idx = np.stack(nz).astype(np.int32)
+    vals = X[nz]
+    return idx, vals, facs
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_cp_als_recovers_exact_rank_r_tensor(seed):
+    dims = (30, 20, 10)
+    R = 3
+    idx, vals, _ = _sparse_ktensor(dims, R, seed)
+    # values stored exactly as float64 here (the oracle takes float64)
+    rng = np.random.default_rng(100 + seed)
+    A = [rng.uniform(0, 1, (I, R)) for I in dims]
+    x2 = float((vals * vals).sum())
+    fits = []
+    for it in range(200):
+        lam, fit, st = oracle.cp_als_iter(idx, vals, dims, A, R, xnorm2=x2)
+        assert st == 0
+        fits.append(fit)
+        if fit > 1 - 1e-7:
+            break
+    assert fits[-1] > 1 - 1e-6, fits[-5:]
+    # ALS never increases the residual (up to rounding)
+    assert all(b >= a - 1e-10 for a, b in zip(fits, fits[1:]))
+
+
+def test_cp_als_fit_and_normal_equations():
+    dims = (9, 8, 7)
+    R = 4
+    idx, vals = synth.coo_uniform_distinct(dims, 150, 3)
+    v64 = vals.astype(np.float64)
+    rng = np.random.default_rng(7)
+    A = [rng.uniform(0, 1, (I, R)) for I in dims]
+    lam, fit, st = oracle.cp_als_iter(idx, v64, dims, A, R)
+    assert st == 0
+    # fit against the dense residual ||X - M|| / ||X||
+    X = _dense(idx, v64, dims)
+    M = np.einsum("r,ir,jr,kr->ijk", lam, *A)
+    ref = 1 - np.linalg.norm(X - M) / np.linalg.norm(X)
+    assert abs(fit - ref) < 1e-10
+    # columns are unit norm, lambda >= 0
+    for f in A:
+        np.testing.assert_allclose(np.linalg.norm(f, axis=0), 1.0, rtol=1e-12)
+    assert (lam >= 0).all()
+    # last mode satisfies its normal equations with the final factors:
+    # MTTKRP_3(X, A) = (A3 diag(lam)) (G1 * G2)
+    V = oracle.mttkrp(idx, v64, dims, A, 2, R)
+    H = (A[0].T @ A[0]) * (A[1].T @ A[1])
+    np.testing.assert_allclose(V, (A[2] * lam[None, :]) @ H, rtol=1e-9, atol=1e-10)
+
+
+def test_cp_als_bf16_rounding_keeps_values_on_bf16_grid():
+    dims = (9, 8, 7)
+    R = 4
+    idx, vals = synth.coo_uniform_distinct(dims, 150, 4)
+    rng = np.random.default_rng(8)
+    A = [rng.uniform(0, 1, (I, R)) for I in dims]
+    oracle.cp_als_iter(idx, vals, dims, A, R, bf16=True)
+    import torch
+    for f in A:
+        t = torch.from_numpy(f.astype(np.float32))
+        back = t.to(torch.bfloat16).to(torch.float64).numpy()
+        np.testing.assert_array_equal(back, f)  # already representable in bf16
+
+
+def test_cp_als_singular_gram_reports_status():
+    dims = (6, 5, 4)
+    R = 3
+    idx, vals = synth.coo_uniform_distinct(dims, 30, 2)
+    # identical columns give rank-1 Grams: the ridge retry rescues the solve
+    A = [np.ones((I, R)) for I in dims]
+    _, _, st = oracle.cp_als_iter(idx, vals, dims, A, R)
+    assert st == 0
+    # all-zero factors give H = 0, which no ridge proportional to trace(H) fixes
+    A = [np.zeros((I, R)) for I in dims]
+    _, _, st = oracle.cp_als_iter(idx, vals, dims, A, R)
+    assert st == 2
+
+
+def _mlp_params(F, H1, H2, K, seed):
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal((H1, F)) * 0.5, rng.standard_normal(H1) * 0.1,
+            rng.standard_normal((H2, H1)) * 0.3, rng.standard_normal(H2) * 0.1,
+            rng.standard_normal((K, H2)) * 0.3, rng.standard_normal(K) * 0.1]
+
+
+def test_mlp_forward_matches_matrix_products():
+    F, H1, H2, K, B = 7, 9, 8, 5, 6
+    p = _mlp_params(F, H1, H2, K, 0)
+    X = np.random.default_rng(1).standard_normal((B, F))
+    relu = lambda z: np.maximum(z, 0)
+    ref = relu(relu(X @ p[0].T + p[1]) @ p[2].T + p[3]) @ p[4].T + p[5]
+    np.testing.assert_allclose(oracle.mlp_forward(X, p), ref, rtol=1e-13, atol=1e-13)
+
+
+def test_mlp_gradient_matches_finite_differences():
+    F, H1, H2, K, B = 5, 6, 7, 4, 8
+    p = _mlp_params(F, H1, H2, K, 2)
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((B, F))
+    T = rng.standard_normal((B, K))
+    M = (rng.random((B, K)) < 0.7).astype(np.float64)
+    loss, grads = oracle.mlp_loss_grad(X, p, T, M)
+    h = 1e-6
+    for pi, (P_, G_) in enumerate(zip(p, grads)):
+        flat = P_.reshape(-1)
+        gflat = G_.reshape(-1)
+        for q in range(flat.size):
+            old = flat[q]
+            flat[q] = old + h
+            lp, _ = oracle.mlp_loss_grad(X, p, T, M)
+            flat[q] = old - h
+            lm, _ = oracle.mlp_loss_grad(X, p, T, M)
+            flat[q] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - gflat[q]) <= 1e-6 * max(1.0, abs(fd)), (pi, q, fd, gflat[q])
