@@ -1,0 +1,220 @@
+/*
+ * spt.h -- C ABI of the GB300 sparse-tensor MTTKRP / CP-ALS library.
+ *
+ * Method: Phipps & Kolda, "Software for Sparse Tensor Decomposition on
+ * Emerging Computing Architectures" (arXiv 1809.09175).  The tensor is a COO
+ * list of P nonzeros x_i with coordinates (l_i1..l_id) (Sec. 2); the kernel
+ * is the mode-n MTTKRP of Sec. 2 eq. (mttkrp); the permuted traversal is
+ * Sec. 5 (Fig. "MTTKRP-C"); CP-ALS is the alternating least squares of Sec. 2.
+ *
+ * Conventions for every call
+ *  - Nothing throws across the ABI.  Every call returns an spt_status; on
+ *    failure spt_last_error() gives a message (per host thread).
+ *  - "device" pointers are CUDA global memory of the current device (for
+ *    example a torch tensor's data_ptr()); "host" pointers are CPU memory.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    stream-ordered and do not synchronise the device, except where a call
+ *    says it does.
+ *  - Coordinates are 0-based int32; P < 2^31; order d in [1, 8] for storage,
+ *    d in [1, 5] for the MTTKRP kernels.
+ *  - Factor matrices are row-major I_m x ld with ld >= rank, ld a multiple
+ *    of 8 elements, base pointer 16-byte aligned.  Element type spt_dtype.
+ *  - Asynchronous CUDA errors surface as SPT_ECUDA at a later call.
+ */
+#ifndef SPT_H
+#define SPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spt_tensor_s *spt_tensor; /* opaque, library-owned */
+
+typedef enum {
+    SPT_OK = 0,
+    SPT_EINVAL = 1,       /* bad argument (null pointer, order, mode, rank, ld, dtype, flags) */
+    SPT_ERANGE = 2,       /* a coordinate outside [0, I_m) */
+    SPT_ENOMEM = 3,       /* device or host allocation failed */
+    SPT_ECUDA = 4,        /* a CUDA runtime call or kernel failed */
+    SPT_EUNSUPPORTED = 5, /* valid request outside what this build implements */
+    SPT_ESINGULAR = 6,    /* normal-equation matrix not positive definite (after ridge retry) */
+    SPT_ETIMEOUT = 7,     /* a bounded device-side wait ran out */
+    SPT_ESTATE = 8        /* the call needs an earlier step (e.g. a coalesced tensor) */
+} spt_status;
+
+typedef enum { SPT_F32 = 0, SPT_BF16 = 1, SPT_F16 = 2 } spt_dtype;
+
+/* tensor_create_coo flags */
+#define SPT_DEVICE_PTRS 1 /* idx / vals are device pointers (copied, not adopted) */
+#define SPT_COALESCE 2    /* sum duplicate coordinates; output in lexicographic order */
+
+/* build_mode_permutation flags */
+#define SPT_PERM_INDEX_ONLY 1 /* keep only the permutation, not the mode-sorted copy */
+
+/* Scatter strategies of the MTTKRP (Sec. 3-5). */
+typedef enum {
+    SPT_SCATTER_AUTO = 0,   /* library choice (learned selector if loaded, else rule) */
+    SPT_SCATTER_ATOMIC = 1, /* storage order, every row flush is an atomic add (Fig. MTTKRP-B) */
+    SPT_SCATTER_PERM = 2,   /* permuted traversal through the mode-n permutation (Fig. MTTKRP-C) */
+    SPT_SCATTER_SORTED = 3  /* permuted traversal over a mode-n-sorted copy of the nonzeros */
+} spt_scatter;
+
+/* A launch schedule of the MTTKRP kernel.
+ *  lanes_per_nnz : 1,2,4,8,16,32 lanes share one nonzero (the paper's
+ *                  vector_size, Tab. "sizes"); groups per warp = 32/lanes.
+ *  chunks        : 1 or 2 sixteen-byte column chunks per lane; the rank
+ *                  block (the paper's FBS) = lanes * chunks * (16 / elem bytes).
+ *  nnz_per_group : nonzeros one lane group walks in order (the paper's
+ *                  NZPTM); adjusted by the library for bank-conflict-free
+ *                  staging.
+ *  warps_per_cta : 1..16.
+ *  ctas_per_sm   : persistent grid = SMs * ctas_per_sm; 0 = occupancy limit. */
+typedef struct {
+    int32_t scatter;
+    int32_t lanes_per_nnz;
+    int32_t chunks;
+    int32_t nnz_per_group;
+    int32_t warps_per_cta;
+    int32_t ctas_per_sm;
+} spt_schedule;
+
+/* ---- errors ---------------------------------------------------------- */
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *spt_last_error(void);
+
+/* ---- tensor ingest (Sec. 2, COO; Sec. 3.2 storage) --------------------- */
+
+/* Create a COO tensor (Sec. 2: a P-vector of values and P x d coordinates).
+ *  order     : d in [1, 8].
+ *  dims      : host, d mode lengths I_m in [1, 2^31 - 1].
+ *  nnz       : P in [0, 2^31 - 1].
+ *  idx       : host array of d pointers; idx[m][i] = l_{i,m} (0-based int32),
+ *              host memory, or device memory with SPT_DEVICE_PTRS.
+ *  vals      : P float32 values x_i (host, or device with SPT_DEVICE_PTRS).
+ *  flags     : SPT_DEVICE_PTRS | SPT_COALESCE.
+ *  out       : receives the handle.
+ * The tensor copies the data into library-owned device memory; the caller
+ * keeps ownership of its buffers.  Coordinates are range-checked on the
+ * device; this call synchronises `stream` to read the check and returns
+ * SPT_ERANGE (creating nothing) if a coordinate is outside [0, I_m).
+ * SPT_COALESCE sums duplicates (Sec. 2: an entry is the sum of the nonzeros
+ * stored at its coordinate), leaving distinct coordinates in lexicographic
+ * order; it is required by cp_als_step, whose fit needs ||X||. */
+spt_status tensor_create_coo(int order, const int64_t *dims, int64_t nnz,
+                             const int32_t *const *idx, const float *vals, int flags,
+                             void *stream, spt_tensor *out);
+
+/* Free a tensor and everything it owns (synchronises the device). */
+spt_status tensor_destroy(spt_tensor t);
+
+/* Shape of a tensor: order, dims (host, >= 8 entries), nnz (after
+ * coalescing), and flags (bit SPT_COALESCE if coalesced). Any output may be NULL. */
+spt_status tensor_info(spt_tensor t, int *order, int64_t *dims, int64_t *nnz, int *flags);
+
+/* Copy the stored nonzeros out to caller device buffers: idx[m] (nnz int32
+ * each, may be NULL to skip a mode) and vals (nnz float32, may be NULL). */
+spt_status tensor_get_coo(spt_tensor t, int32_t *const *idx, float *vals, void *stream);
+
+/* ||X||^2 in FP64 for a coalesced tensor (SPT_ESTATE otherwise). Host output. */
+spt_status tensor_norm2(spt_tensor t, double *out);
+
+/* Synchronise `stream` and read the tensor's device status word: SPT_OK, or
+ * SPT_ETIMEOUT if a kernel's bounded wait ran out since the tensor was made. */
+spt_status tensor_check(spt_tensor t, void *stream);
+
+/* ---- mode permutations (Sec. 5) --------------------------------------- */
+
+/* Build the mode-n permutation of Sec. 5: perm_n lists nonzero positions in
+ * increasing mode-n coordinate, ties in storage order (a stable sort, done
+ * by an on-device LSD radix sort).  mode = -1 builds all modes.  Unless
+ * flags has SPT_PERM_INDEX_ONLY, the nonzeros are also copied in perm_n
+ * order (a mode-sorted copy) so SPT_SCATTER_SORTED can stream them.
+ * Also records per-mode slice statistics used by the schedule selector.
+ * Memory: 4P bytes per mode for perm_n, plus (4d + 4)P for the copy; the
+ * radix sort borrows 16P bytes of temporary device memory. */
+spt_status build_mode_permutation(spt_tensor t, int mode, int flags, void *stream);
+
+/* Copy perm_n (P int32) to a caller device buffer. SPT_ESTATE if not built. */
+spt_status tensor_get_permutation(spt_tensor t, int mode, int32_t *perm, void *stream);
+
+/* ---- MTTKRP (Sec. 2 eq. mttkrp; Figs. MTTKRP-A/B/C) -------------------- */
+
+/* Mode-n MTTKRP:  out(k, j) = lambda_j * sum_{i : l_in = k} x_i *
+ *                             prod_{m != n} A^(m)(l_im, j)
+ * for k < I_n, j < rank.
+ *  factors : host array of d device pointers; factors[m] is A^(m), row-major
+ *            I_m x ld of type fdt.  factors[mode] is not read (may be NULL).
+ *  rank    : R >= 1.  ld : row stride of the factors and of out (elements,
+ *            multiple of 8, >= rank).
+ *  lambda  : device, rank float32 weights, or NULL for all ones.
+ *  out     : device float32 I_n x ld; overwritten (columns >= rank set to 0).
+ *  sched   : NULL = library choice; else the schedule to run (SPT_SCATTER_PERM
+ *            and SPT_SCATTER_SORTED need build_mode_permutation(mode)).
+ * Accumulation is float32.  The atomic and permuted strategies add in
+ * different orders, so results agree to rounding, not bit for bit. */
+spt_status mttkrp(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt, int rank,
+                  int ld, const float *lambda, float *out, const spt_schedule *sched,
+                  void *stream);
+
+/* The schedule mttkrp() runs for sched == NULL (host logic, no launch). */
+spt_status mttkrp_default_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank,
+                                   spt_schedule *out);
+
+/* Tab. "sizes" (Sec. 4): the GPU vector_size and factor block size FBS the
+ * paper uses for rank R. Host logic. */
+spt_status mttkrp_paper_sizes(int rank, int *vector_size, int *fbs);
+
+/* The paper's fixed rule (Tab. "sizes": vector_size and FBS as functions of R),
+ * mapped onto this kernel's schedule for the given scatter strategy. */
+spt_status mttkrp_paper_schedule(int rank, spt_dtype fdt, int scatter, spt_schedule *out);
+
+/* ---- CP-ALS (Sec. 2) -------------------------------------------------- */
+
+/* Workspace bytes cp_als_step needs for this tensor, rank and ld. */
+spt_status cp_als_workspace_size(spt_tensor t, int rank, int ld, size_t *bytes);
+
+/* One CP-ALS iteration over all modes n = 0..d-1 in order (Sec. 2, ALS):
+ *   V = MTTKRP_n(X, A) (unit weights); H = elementwise product over m != n of
+ *   A^(m)T A^(m) (FP64); Cholesky H = L L^T (FP64, one retry with a ridge of
+ *   1e-12 trace(H)/R); A^(n) = V H^-1; lambda_j = ||A^(n)(:,j)||_2 (FP64) and
+ *   A^(n)(:,j) /= lambda_j; 16-bit factors are rounded (nearest even) after
+ *   normalising.  After the last mode, fit = 1 - ||X - M|| / ||X|| with
+ *   ||M||^2 = lambda^T (*_m G_m) lambda and <X, M> = sum_{k,j} V(k,j) lambda_j
+ *   A^(d)(k,j) from the last mode's V (FP64 reductions).
+ *  factors   : host array of d device pointers, I_m x ld, type fdt; updated.
+ *  lambda    : device, rank doubles (output).
+ *  fit_out   : device double (output) or NULL.
+ *  workspace : device, >= cp_als_workspace_size() bytes, 256-byte aligned.
+ * Needs a coalesced tensor (SPT_ESTATE) and rank <= 128 (SPT_EUNSUPPORTED).
+ * SPT_ESINGULAR is reported by the next call (or cp_als_status) because the
+ * solve runs on the device; the factors of a singular mode are left as V. */
+spt_status cp_als_step(spt_tensor t, void *const *factors, spt_dtype fdt, int rank, int ld,
+                       double *lambda, double *fit_out, void *workspace, size_t workspace_bytes,
+                       void *stream);
+
+/* Device status word of the last cp_als_step on this workspace (synchronises
+ * `stream`): SPT_OK or SPT_ESINGULAR. */
+spt_status cp_als_status(void *workspace, void *stream);
+
+/* ---- utilities -------------------------------------------------------- */
+
+/* STREAM-style copy dst[0:bytes) = src[0:bytes) with this library's own
+ * kernel (16-byte vector loads/stores, persistent grid); the bandwidth
+ * denominator of Sec. 6 ("peak bandwidth via STREAM"). bytes % 16 == 0,
+ * both pointers 16-byte aligned. */
+spt_status spt_stream_copy(const void *src, void *dst, size_t bytes, void *stream);
+
+/* Convert n float32 values to fdt storage (round to nearest even). */
+spt_status spt_convert_f32(const float *src, void *dst, spt_dtype fdt, int64_t n, void *stream);
+
+/* Number of SMs of the current device and this library's build arch (e.g. 103). */
+spt_status spt_device_info(int *sm_count, int *arch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPT_H */

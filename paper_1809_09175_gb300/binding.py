@@ -1,0 +1,228 @@
+"""ctypes binding of ``libspt.so`` -- argument marshalling only.
+
+Each function has the name of the C entry point it calls (declared in
+``include/spt.h``) and takes plain integers for device pointers (for example
+``torch_tensor.data_ptr()``) and CUDA streams (``torch.cuda.current_stream()
+.cuda_stream``).  A non-zero status raises :class:`SptError`.  There is no
+fallback: if the compiled library is missing, importing this module fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libspt.so")
+
+SPT_OK, SPT_EINVAL, SPT_ERANGE, SPT_ENOMEM, SPT_ECUDA = 0, 1, 2, 3, 4
+SPT_EUNSUPPORTED, SPT_ESINGULAR, SPT_ETIMEOUT, SPT_ESTATE = 5, 6, 7, 8
+SPT_F32, SPT_BF16, SPT_F16 = 0, 1, 2
+SPT_DEVICE_PTRS, SPT_COALESCE = 1, 2
+SPT_PERM_INDEX_ONLY = 1
+SPT_SCATTER_AUTO, SPT_SCATTER_ATOMIC, SPT_SCATTER_PERM, SPT_SCATTER_SORTED = 0, 1, 2, 3
+
+STATUS_NAMES = {0: "SPT_OK", 1: "SPT_EINVAL", 2: "SPT_ERANGE", 3: "SPT_ENOMEM", 4: "SPT_ECUDA",
+                5: "SPT_EUNSUPPORTED", 6: "SPT_ESINGULAR", 7: "SPT_ETIMEOUT", 8: "SPT_ESTATE"}
+DTYPES = {"f32": SPT_F32, "bf16": SPT_BF16, "f16": SPT_F16}
+SCATTERS = {"auto": SPT_SCATTER_AUTO, "atomic": SPT_SCATTER_ATOMIC, "perm": SPT_SCATTER_PERM,
+            "sorted": SPT_SCATTER_SORTED}
+
+
+class SptError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class spt_schedule(C.Structure):
+    _fields_ = [("scatter", C.c_int32), ("lanes_per_nnz", C.c_int32), ("chunks", C.c_int32),
+                ("nnz_per_group", C.c_int32), ("warps_per_cta", C.c_int32),
+                ("ctas_per_sm", C.c_int32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+    @classmethod
+    def make(cls, scatter=SPT_SCATTER_AUTO, lanes_per_nnz=4, chunks=1, nnz_per_group=32,
+             warps_per_cta=8, ctas_per_sm=0):
+        if isinstance(scatter, str):
+            scatter = SCATTERS[scatter]
+        return cls(scatter, lanes_per_nnz, chunks, nnz_per_group, warps_per_cta, ctas_per_sm)
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: run paper_1809_09175_gb300/build.py (or "
+                      "__graft_entry__.build()) to compile the CUDA library")
+
+_L = C.CDLL(LIB_PATH)
+_vp = C.c_void_p
+_i64p = C.POINTER(C.c_int64)
+
+
+def _sig(name, *args):
+    f = getattr(_L, name)
+    f.argtypes = list(args)
+    f.restype = C.c_int
+    return f
+
+
+_L.spt_last_error.restype = C.c_char_p
+_L.spt_last_error.argtypes = []
+_sig("spt_device_info", C.POINTER(C.c_int), C.POINTER(C.c_int))
+_sig("tensor_create_coo", C.c_int, _i64p, C.c_int64, C.POINTER(_vp), _vp, C.c_int, _vp,
+     C.POINTER(_vp))
+_sig("tensor_destroy", _vp)
+_sig("tensor_info", _vp, C.POINTER(C.c_int), _i64p, _i64p, C.POINTER(C.c_int))
+_sig("tensor_get_coo", _vp, C.POINTER(_vp), _vp, _vp)
+_sig("tensor_norm2", _vp, C.POINTER(C.c_double))
+_sig("tensor_check", _vp, _vp)
+_sig("build_mode_permutation", _vp, C.c_int, C.c_int, _vp)
+_sig("tensor_get_permutation", _vp, C.c_int, _vp, _vp)
+_sig("mttkrp", _vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _vp, _vp,
+     C.POINTER(spt_schedule), _vp)
+_sig("mttkrp_default_schedule", _vp, C.c_int, C.c_int, C.c_int, C.POINTER(spt_schedule))
+_sig("mttkrp_paper_sizes", C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int))
+_sig("mttkrp_paper_schedule", C.c_int, C.c_int, C.c_int, C.POINTER(spt_schedule))
+_sig("spt_stream_copy", _vp, _vp, C.c_size_t, _vp)
+_sig("spt_convert_f32", _vp, _vp, C.c_int, C.c_int64, _vp)
+
+EXPORTED = ["spt_last_error", "spt_device_info", "tensor_create_coo", "tensor_destroy",
+            "tensor_info", "tensor_get_coo", "tensor_norm2", "tensor_check",
+            "build_mode_permutation", "tensor_get_permutation", "mttkrp",
+            "mttkrp_default_schedule", "mttkrp_paper_sizes", "mttkrp_paper_schedule",
+            "spt_stream_copy", "spt_convert_f32"]
+
+
+def _try_sig(name, *args):
+    if hasattr(_L, name):
+        _sig(name, *args)
+        EXPORTED.append(name)
+
+
+# CP-ALS and later entry points (declared when present in the library)
+_try_sig("cp_als_workspace_size", _vp, C.c_int, C.c_int, C.POINTER(C.c_size_t))
+_try_sig("cp_als_step", _vp, C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _vp, _vp, _vp,
+         C.c_size_t, _vp)
+_try_sig("cp_als_status", _vp, _vp)
+
+
+def lib():
+    return _L
+
+
+def _chk(st: int):
+    if st != SPT_OK:
+        raise SptError(st, _L.spt_last_error().decode())
+
+
+def spt_last_error() -> str:
+    return _L.spt_last_error().decode()
+
+
+def _ptrs(ps: Sequence[Optional[int]]):
+    return (_vp * len(ps))(*[p if p else None for p in ps])
+
+
+def _dt(fdt):
+    return DTYPES[fdt] if isinstance(fdt, str) else int(fdt)
+
+
+def spt_device_info():
+    sm, arch = C.c_int(), C.c_int()
+    _chk(_L.spt_device_info(C.byref(sm), C.byref(arch)))
+    return sm.value, arch.value
+
+
+def tensor_create_coo(order: int, dims: Sequence[int], nnz: int, idx_ptrs: Sequence[int],
+                      vals_ptr: int, flags: int = 0, stream: int = 0) -> int:
+    """Returns the tensor handle (an integer)."""
+    dims_a = (C.c_int64 * order)(*[int(x) for x in dims])
+    out = _vp()
+    _chk(_L.tensor_create_coo(order, dims_a, int(nnz), _ptrs(idx_ptrs), vals_ptr or None, flags,
+                              stream or None, C.byref(out)))
+    return out.value
+
+
+def tensor_destroy(t: int):
+    _chk(_L.tensor_destroy(t))
+
+
+def tensor_info(t: int):
+    order, flags = C.c_int(), C.c_int()
+    dims = (C.c_int64 * 8)()
+    nnz = C.c_int64()
+    _chk(_L.tensor_info(t, C.byref(order), dims, C.byref(nnz), C.byref(flags)))
+    return order.value, [int(dims[m]) for m in range(order.value)], nnz.value, flags.value
+
+
+def tensor_get_coo(t: int, idx_ptrs: Sequence[Optional[int]], vals_ptr: Optional[int], stream: int = 0):
+    _chk(_L.tensor_get_coo(t, _ptrs(idx_ptrs), vals_ptr or None, stream or None))
+
+
+def tensor_norm2(t: int) -> float:
+    v = C.c_double()
+    _chk(_L.tensor_norm2(t, C.byref(v)))
+    return v.value
+
+
+def tensor_check(t: int, stream: int = 0):
+    _chk(_L.tensor_check(t, stream or None))
+
+
+def build_mode_permutation(t: int, mode: int = -1, flags: int = 0, stream: int = 0):
+    _chk(_L.build_mode_permutation(t, mode, flags, stream or None))
+
+
+def tensor_get_permutation(t: int, mode: int, perm_ptr: int, stream: int = 0):
+    _chk(_L.tensor_get_permutation(t, mode, perm_ptr, stream or None))
+
+
+def mttkrp(t: int, mode: int, factor_ptrs: Sequence[Optional[int]], fdt, rank: int, ld: int,
+           lambda_ptr: Optional[int], out_ptr: int, sched: Optional[spt_schedule] = None,
+           stream: int = 0):
+    _chk(_L.mttkrp(t, mode, _ptrs(factor_ptrs), _dt(fdt), rank, ld, lambda_ptr or None, out_ptr,
+                   C.byref(sched) if sched is not None else None, stream or None))
+
+
+def mttkrp_default_schedule(t: int, mode: int, fdt, rank: int) -> spt_schedule:
+    s = spt_schedule()
+    _chk(_L.mttkrp_default_schedule(t, mode, _dt(fdt), rank, C.byref(s)))
+    return s
+
+
+def mttkrp_paper_sizes(rank: int):
+    vs, fbs = C.c_int(), C.c_int()
+    _chk(_L.mttkrp_paper_sizes(rank, C.byref(vs), C.byref(fbs)))
+    return vs.value, fbs.value
+
+
+def mttkrp_paper_schedule(rank: int, fdt, scatter) -> spt_schedule:
+    s = spt_schedule()
+    sc = SCATTERS[scatter] if isinstance(scatter, str) else int(scatter)
+    _chk(_L.mttkrp_paper_schedule(rank, _dt(fdt), sc, C.byref(s)))
+    return s
+
+
+def spt_stream_copy(src_ptr: int, dst_ptr: int, nbytes: int, stream: int = 0):
+    _chk(_L.spt_stream_copy(src_ptr, dst_ptr, nbytes, stream or None))
+
+
+def spt_convert_f32(src_ptr: int, dst_ptr: int, fdt, n: int, stream: int = 0):
+    _chk(_L.spt_convert_f32(src_ptr, dst_ptr, _dt(fdt), n, stream or None))
+
+
+def cp_als_workspace_size(t: int, rank: int, ld: int) -> int:
+    v = C.c_size_t()
+    _chk(_L.cp_als_workspace_size(t, rank, ld, C.byref(v)))
+    return v.value
+
+
+def cp_als_step(t: int, factor_ptrs: Sequence[int], fdt, rank: int, ld: int, lambda_ptr: int,
+                fit_ptr: Optional[int], workspace_ptr: int, workspace_bytes: int, stream: int = 0):
+    _chk(_L.cp_als_step(t, _ptrs(factor_ptrs), _dt(fdt), rank, ld, lambda_ptr, fit_ptr or None,
+                        workspace_ptr, workspace_bytes, stream or None))
+
+
+def cp_als_status(workspace_ptr: int, stream: int = 0):
+    _chk(_L.cp_als_status(workspace_ptr, stream or None))

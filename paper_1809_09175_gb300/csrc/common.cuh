@@ -1,0 +1,168 @@
+// common.cuh -- internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/spt.h"
+
+#define SPT_MAX_ORDER 8
+#define SPT_MAX_KERNEL_ORDER 5
+
+// Device-side error codes written to a status word (never a trap).
+#define SPT_DEV_OK 0
+#define SPT_DEV_TIMEOUT 1
+#define SPT_DEV_SINGULAR 2
+
+// Iteration limit of every bounded spin-wait: each try_wait suspends for at
+// most ~1 us (the hint below), so this bounds a wait to a few seconds.
+#define SPT_WAIT_TRIES (1u << 22)
+#define SPT_WAIT_HINT_NS 1000u
+
+struct ModeStats {
+    bool valid = false;
+    int64_t nonempty = 0;   // rows with at least one nonzero
+    int64_t max_count = 0;  // nonzeros in the hottest row
+    double sum_sq = 0.0;    // sum over rows of count^2
+    int64_t runs_storage = 0; // row changes along storage order (+1)
+};
+
+struct spt_tensor_s {
+    int device = 0;
+    int d = 0;
+    int64_t dims[SPT_MAX_ORDER] = {0};
+    int64_t nnz = 0;
+    bool coalesced = false;
+    double xnorm2 = 0.0;
+    // storage-order COO: one allocation, d index arrays then the values,
+    // each segment 256-byte aligned.
+    void *coo_buf = nullptr;
+    int32_t *idx[SPT_MAX_ORDER] = {nullptr};
+    float *vals = nullptr;
+    // per mode: permutation and optional mode-sorted copy (d index arrays + values)
+    int32_t *perm[SPT_MAX_ORDER] = {nullptr};
+    void *sorted_buf[SPT_MAX_ORDER] = {nullptr};
+    int32_t *sidx[SPT_MAX_ORDER][SPT_MAX_ORDER] = {{nullptr}};
+    float *svals[SPT_MAX_ORDER] = {nullptr};
+    ModeStats stats[SPT_MAX_ORDER];
+    int *dev_err = nullptr;  // device status word for kernels of this tensor
+};
+
+// ---- host error handling -------------------------------------------------
+namespace spt {
+void set_error(const std::string &msg);
+spt_status fail(spt_status st, const std::string &msg);
+spt_status cuda_fail(cudaError_t e, const char *what);
+int sm_count();
+size_t seg_bytes(int64_t n, size_t elem);  // n*elem rounded up to 256
+}  // namespace spt
+
+#define SPT_CUDA(call)                                              \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return spt::cuda_fail(e_, #call);    \
+    } while (0)
+
+#define SPT_LAUNCH_CHECK(what)                                      \
+    do {                                                            \
+        cudaError_t e_ = cudaGetLastError();                        \
+        if (e_ != cudaSuccess) return spt::cuda_fail(e_, what);     \
+    } while (0)
+
+// ---- device helpers --------------------------------------------------------
+namespace spt {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+// 1-D bulk copy global -> shared (this CTA), completion counted on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bounded wait for phase `parity` of `bar`.  Returns true when the phase
+// completed, false when the try budget ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t addr = smem_u32(bar);
+    for (uint32_t it = 0; it < SPT_WAIT_TRIES; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity), "r"(SPT_WAIT_HINT_NS)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+// Element traits: 16 bytes of factor row = VEC elements, widened to float.
+template <typename T> struct Elem;
+template <> struct Elem<float> {
+    static constexpr int VEC = 4;
+    static constexpr int BYTES = 4;
+    __device__ __forceinline__ static void widen(const uint4 &r, float *o) {
+        o[0] = __uint_as_float(r.x); o[1] = __uint_as_float(r.y);
+        o[2] = __uint_as_float(r.z); o[3] = __uint_as_float(r.w);
+    }
+};
+template <> struct Elem<__nv_bfloat16> {
+    static constexpr int VEC = 8;
+    static constexpr int BYTES = 2;
+    __device__ __forceinline__ static void widen(const uint4 &r, float *o) {
+        o[0] = bf16_lo(r.x); o[1] = bf16_hi(r.x); o[2] = bf16_lo(r.y); o[3] = bf16_hi(r.y);
+        o[4] = bf16_lo(r.z); o[5] = bf16_hi(r.z); o[6] = bf16_lo(r.w); o[7] = bf16_hi(r.w);
+    }
+};
+template <> struct Elem<__half> {
+    static constexpr int VEC = 8;
+    static constexpr int BYTES = 2;
+    __device__ __forceinline__ static void widen(const uint4 &r, float *o) {
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            __half2 h = *reinterpret_cast<const __half2 *>(&w[q]);
+            float2 f = __half22float2(h);
+            o[2 * q] = f.x;
+            o[2 * q + 1] = f.y;
+        }
+    }
+};
+
+}  // namespace spt

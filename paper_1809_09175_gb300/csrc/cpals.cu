@@ -1,0 +1,470 @@
+// cpals.cu -- one CP-ALS iteration on the device (Sec. 2: alternating least
+// squares; the MTTKRP of Sec. 2 eq. mttkrp is its dominant step).
+//
+// Per mode n (in order 0..d-1):
+//   1. V = MTTKRP_n(X, A)                                (mttkrp kernel)
+//   2. H = *_{m != n} G_m, Cholesky H = L L^T, W = L^-1,
+//      Hinv = W^T W                                       (one CTA, FP64)
+//   3. A32 = V Hinv, colsq_j = sum_k A32(k,j)^2           (FP32 FMAs, FP64 sums)
+//   4. lambda_j = sqrt(colsq_j), A^(n) = A32 / lambda   -> stored type
+//      (round to nearest even for 16-bit factors)
+//   5. G_n = A^(n)T A^(n) of the stored values           (FP32 partials over
+//      row tiles, accumulated in FP64)
+// After the last mode: fit = 1 - sqrt(max(0, ||X||^2 + ||M||^2 - 2<X,M>))/||X||
+// with ||M||^2 = lambda^T (*_m G_m) lambda and <X,M> = sum V(k,j) lambda_j
+// A^(d)(k,j) over the last mode's V.
+//
+// GB300 has little FP64 throughput, so FP64 is kept to the R x R work and to
+// reductions; every O(I R^2) loop runs FP32 FMAs with FP64 accumulation of
+// short partial sums.
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "internal.h"
+
+namespace spt {
+namespace {
+
+constexpr int MAXR = 128;
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename FT> __device__ __forceinline__ float ld_elem(const FT *p);
+template <> __device__ __forceinline__ float ld_elem<float>(const float *p) { return *p; }
+template <> __device__ __forceinline__ float ld_elem<__nv_bfloat16>(const __nv_bfloat16 *p) {
+    return __bfloat162float(*p);
+}
+template <> __device__ __forceinline__ float ld_elem<__half>(const __half *p) { return __half2float(*p); }
+
+template <typename FT> __device__ __forceinline__ FT st_elem(float v);
+template <> __device__ __forceinline__ float st_elem<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 st_elem<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ __half st_elem<__half>(float v) { return __float2half_rn(v); }
+
+// G += A^T A over all I rows (A row-major, stride ld, first R columns).
+// Thread t owns entries t + k*blockDim of the R x R result.  Rows are staged
+// 32 at a time in shared memory; FP32 partial sums over 256 rows are folded
+// into FP64 accumulators, and each CTA adds its FP64 result atomically.
+template <typename FT, int PPT>
+__global__ void __launch_bounds__(512) gram_kernel(const FT *A, int64_t I, int ld, int R, double *G) {
+    constexpr int TR = 32;
+    __shared__ float s[TR][MAXR + 1];
+    const int RR = R * R;
+    float acc[PPT];
+    double dacc[PPT];
+    int pp[PPT], qq[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        acc[k] = 0.f;
+        dacc[k] = 0.0;
+        const int e = threadIdx.x + k * blockDim.x;
+        pp[k] = e < RR ? e / R : 0;
+        qq[k] = e < RR ? e % R : 0;
+    }
+    int since = 0;
+    for (int64_t r0 = (int64_t)blockIdx.x * TR; r0 < I; r0 += (int64_t)gridDim.x * TR) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < TR * R; e += blockDim.x) {
+            const int r = e / R, c = e % R;
+            s[r][c] = (r0 + r < I) ? ld_elem<FT>(A + (r0 + r) * ld + c) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < TR; ++r) {
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) acc[k] = fmaf(s[r][pp[k]], s[r][qq[k]], acc[k]);
+        }
+        since += TR;
+        if (since >= 256) {
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) { dacc[k] += (double)acc[k]; acc[k] = 0.f; }
+            since = 0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int e = threadIdx.x + k * blockDim.x;
+        if (e < RR) atomicAdd(G + e, dacc[k] + (double)acc[k]);
+    }
+}
+
+// H = *_{m != n} G_m; zero G_n and the column sums for this mode's update;
+// Cholesky (one retry with ridge 1e-12 trace/R); Hinv = L^-T L^-1 -> float.
+// Shared memory: R*R doubles (L in the lower triangle, W = L^-1 strictly
+// below the diagonal stored transposed in the upper triangle) + R doubles.
+__global__ void __launch_bounds__(512) chol_inv_kernel(double *G, int d, int n, int R, float *Hinv,
+                                                       double *colsq, int *status) {
+    extern __shared__ double sh[];
+    double *Hs = sh;            // R x R
+    double *Wd = sh + R * R;    // R: diagonal of W
+    __shared__ int fail;
+    __shared__ double ridge;
+    const int RR = R * R;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+            double h = 1.0;
+            for (int m = 0; m < d; ++m)
+                if (m != n) h *= G[(int64_t)m * RR + e];
+            Hs[e] = h;
+        }
+        if (threadIdx.x == 0) fail = 0;
+        __syncthreads();
+        if (attempt == 1) {
+            if (threadIdx.x == 0) {
+                double tr = 0.0;
+                for (int r = 0; r < R; ++r) tr += Hs[r * R + r];
+                ridge = 1e-12 * tr / R;
+            }
+            __syncthreads();
+            for (int r = threadIdx.x; r < R; r += blockDim.x) Hs[r * R + r] += ridge;
+            __syncthreads();
+        }
+        for (int k = 0; k < R; ++k) {
+            if (threadIdx.x == 0) {
+                const double p = Hs[k * R + k];
+                if (!(p > 0.0)) fail = 1;
+                Hs[k * R + k] = p > 0.0 ? sqrt(p) : 1.0;
+            }
+            __syncthreads();
+            if (fail) break;
+            const double lkk = Hs[k * R + k];
+            for (int i = k + 1 + threadIdx.x; i < R; i += blockDim.x) Hs[i * R + k] /= lkk;
+            __syncthreads();
+            const int rem = R - k - 1;
+            for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+                const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+                if (j <= i) Hs[i * R + j] -= Hs[i * R + k] * Hs[j * R + k];
+            }
+            __syncthreads();
+        }
+        if (!fail) break;
+    }
+    if (fail) {
+        // not positive definite after the ridge: report, leave the mode's
+        // factor as V (Hinv = identity)
+        if (threadIdx.x == 0) atomicExch(status, SPT_DEV_SINGULAR);
+        for (int e = threadIdx.x; e < RR; e += blockDim.x) Hinv[e] = (e / R == e % R) ? 1.f : 0.f;
+    } else {
+        // W = L^-1 by forward substitution, one column per thread
+        for (int c = threadIdx.x; c < R; c += blockDim.x) {
+            Wd[c] = 1.0 / Hs[c * R + c];
+            for (int i = c + 1; i < R; ++i) {
+                double sacc = Hs[i * R + c] * Wd[c];
+                for (int k = c + 1; k < i; ++k) sacc += Hs[i * R + k] * Hs[c * R + k];
+                Hs[c * R + i] = -sacc / Hs[i * R + i];  // W[i][c] stored at (c, i)
+            }
+        }
+        __syncthreads();
+        // Hinv(i,j) = sum_{k >= max(i,j)} W[k][i] W[k][j]
+        for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+            const int i = e / R, j = e % R;
+            const int k0 = i > j ? i : j;
+            double sacc = 0.0;
+            for (int k = k0; k < R; ++k) {
+                const double wi = (k == i) ? Wd[i] : Hs[i * R + k];
+                const double wj = (k == j) ? Wd[j] : Hs[j * R + k];
+                sacc += wi * wj;
+            }
+            Hinv[e] = (float)sacc;
+        }
+    }
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) G[(int64_t)n * RR + e] = 0.0;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) colsq[r] = 0.0;
+}
+
+// A32 = V Hinv (rows of V staged in shared memory), column sums of squares.
+__global__ void __launch_bounds__(256) solve_kernel(const float *V, int64_t I, int ld, int R,
+                                                    const float *Hinv, float *A32, double *colsq) {
+    extern __shared__ float shs[];
+    float *Hs = shs;                 // R x R
+    const int rows = blockDim.x / R;  // rows per tile (R divides 256 or R > 128 never)
+    float *Vs = shs + R * R;          // rows x R
+    __shared__ double csq[MAXR];
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) Hs[e] = Hinv[e];
+    for (int e = threadIdx.x; e < R; e += blockDim.x) csq[e] = 0.0;
+    const int tr = threadIdx.x / R, j = threadIdx.x % R;
+    const bool act = tr < rows;
+    double local = 0.0;
+    for (int64_t r0 = (int64_t)blockIdx.x * rows; r0 < I; r0 += (int64_t)gridDim.x * rows) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
+            const int r = e / R, c = e % R;
+            Vs[e] = (r0 + r < I) ? V[(r0 + r) * ld + c] : 0.f;
+        }
+        __syncthreads();
+        if (act && r0 + tr < I) {
+            float a = 0.f;
+            const float *vr = Vs + tr * R;
+#pragma unroll 8
+            for (int i = 0; i < R; ++i) a = fmaf(vr[i], Hs[i * R + j], a);
+            A32[(r0 + tr) * ld + j] = a;
+            local += (double)a * (double)a;
+        }
+    }
+    if (act) atomicAdd(&csq[j], local);
+    __syncthreads();
+    for (int e = threadIdx.x; e < R; e += blockDim.x) atomicAdd(colsq + e, csq[e]);
+}
+
+// lambda_j = ||A32(:,j)||, store A32/lambda in the factor's type (padding
+// columns zero); on the last mode accumulate <X,M> = sum V(k,j) lambda_j A(k,j).
+template <typename FT>
+__global__ void normalize_kernel(const float *A32, const float *V, int64_t I, int ld, int R,
+                                 const double *colsq, FT *A, double *lambda, int last,
+                                 double *inner) {
+    double local = 0.0;
+    const int64_t total = I * ld;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e % ld);
+        float out = 0.f;
+        if (j < R) {
+            const double lam = sqrt(colsq[j]);
+            const float a = A32[e];
+            out = lam > 0.0 ? (float)((double)a / lam) : a;
+            const FT st = st_elem<FT>(out);
+            A[e] = st;
+            if (last) local += (double)V[e] * lam * (double)ld_elem<FT>(&st);
+        } else {
+            A[e] = st_elem<FT>(0.f);
+        }
+    }
+    if (blockIdx.x == 0)
+        for (int j = threadIdx.x; j < R; j += blockDim.x) lambda[j] = sqrt(colsq[j]);
+    if (last) {
+        for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(FULL, local, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(inner, local);
+    }
+}
+
+// fit from lambda, the Grams, <X,M> and ||X||^2 (one CTA).
+__global__ void fit_kernel(const double *G, int d, int R, const double *lambda, double *inner,
+                           double x2, double *fit_out) {
+    __shared__ double red[32];
+    double local = 0.0;
+    const int RR = R * R;
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+        double h = lambda[e / R] * lambda[e % R];
+        for (int m = 0; m < d; ++m) h *= G[(int64_t)m * RR + e];
+        local += h;
+    }
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(FULL, local, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 += red[w];
+        double r2 = x2 + m2 - 2.0 * (*inner);
+        if (r2 < 0.0) r2 = 0.0;
+        if (fit_out) *fit_out = x2 > 0.0 ? 1.0 - sqrt(r2) / sqrt(x2) : 0.0;
+        *inner = 0.0;  // ready for the next iteration
+    }
+}
+
+struct Ws {
+    float *V, *A32, *Hinv;
+    double *G, *colsq, *inner;
+    int *status;
+};
+
+size_t ws_layout(spt_tensor t, int R, int ld, Ws *w, void *base) {
+    int64_t imax = 1;
+    for (int m = 0; m < t->d; ++m) imax = std::max(imax, t->dims[m]);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    const size_t oS = take(sizeof(int));  // status word first: cp_als_status reads offset 0
+    const size_t oV = take(sizeof(float) * imax * ld);
+    const size_t oA = take(sizeof(float) * imax * ld);
+    const size_t oH = take(sizeof(float) * R * R);
+    const size_t oG = take(sizeof(double) * t->d * R * R);
+    const size_t oC = take(sizeof(double) * R);
+    const size_t oI = take(sizeof(double));
+    if (w && base) {
+        char *b = (char *)base;
+        w->V = (float *)(b + oV);
+        w->A32 = (float *)(b + oA);
+        w->Hinv = (float *)(b + oH);
+        w->G = (double *)(b + oG);
+        w->colsq = (double *)(b + oC);
+        w->inner = (double *)(b + oI);
+        w->status = (int *)(b + oS);
+    }
+    return off;
+}
+
+template <typename FT>
+spt_status launch_gram(const void *A, int64_t I, int ld, int R, double *G, cudaStream_t st) {
+    const int blocks = sm_count() * 2;
+    if (R <= 16) gram_kernel<FT, 1><<<blocks, 256, 0, st>>>((const FT *)A, I, ld, R, G);
+    else if (R <= 32) gram_kernel<FT, 4><<<blocks, 256, 0, st>>>((const FT *)A, I, ld, R, G);
+    else if (R <= 64) gram_kernel<FT, 16><<<blocks, 256, 0, st>>>((const FT *)A, I, ld, R, G);
+    else gram_kernel<FT, 32><<<blocks, 512, 0, st>>>((const FT *)A, I, ld, R, G);
+    SPT_LAUNCH_CHECK("gram_kernel");
+    return SPT_OK;
+}
+
+spt_status gram_any(spt_dtype fdt, const void *A, int64_t I, int ld, int R, double *G, cudaStream_t st) {
+    if (fdt == SPT_F32) return launch_gram<float>(A, I, ld, R, G, st);
+    if (fdt == SPT_BF16) return launch_gram<__nv_bfloat16>(A, I, ld, R, G, st);
+    return launch_gram<__half>(A, I, ld, R, G, st);
+}
+
+// Enqueue one iteration (no synchronisation, capturable).
+spt_status enqueue_step(spt_tensor t, void *const *factors, spt_dtype fdt, int R, int ld,
+                        double *lambda, double *fit_out, const Ws &w, cudaStream_t st) {
+    const int d = t->d;
+    SPT_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * d * R * R, st));
+    SPT_CUDA(cudaMemsetAsync(w.inner, 0, sizeof(double), st));
+    SPT_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), st));
+    for (int m = 0; m < d; ++m) {
+        spt_status s = gram_any(fdt, factors[m], t->dims[m], ld, R, w.G + (size_t)m * R * R, st);
+        if (s) return s;
+    }
+    static bool attr_set = false;
+    const size_t chol_smem = sizeof(double) * (R * R + R);
+    if (!attr_set) {
+        SPT_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      sizeof(double) * (MAXR * MAXR + MAXR)));
+        SPT_CUDA(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      sizeof(float) * (MAXR * MAXR + 256)));
+        attr_set = true;
+    }
+    for (int n = 0; n < d; ++n) {
+        const int64_t In = t->dims[n];
+        spt_schedule sc = default_schedule(t, n, fdt, R);
+        spt_status s = launch_mttkrp(t, n, factors, fdt, R, ld, nullptr, w.V, sc, st);
+        if (s) return s;
+        chol_inv_kernel<<<1, 512, chol_smem, st>>>(w.G, d, n, R, w.Hinv, w.colsq, w.status);
+        SPT_LAUNCH_CHECK("chol_inv_kernel");
+        const int rows = 256 / R;
+        const size_t solve_smem = sizeof(float) * (R * R + rows * R);
+        const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((In + rows - 1) / rows, sm_count() * 4));
+        solve_kernel<<<sblocks, 256, solve_smem, st>>>(w.V, In, ld, R, w.Hinv, w.A32, w.colsq);
+        SPT_LAUNCH_CHECK("solve_kernel");
+        const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>((In * ld + 255) / 256, sm_count() * 8));
+        const int last = (n == d - 1);
+        if (fdt == SPT_F32)
+            normalize_kernel<float><<<nblocks, 256, 0, st>>>(w.A32, w.V, In, ld, R, w.colsq,
+                                                             (float *)factors[n], lambda, last, w.inner);
+        else if (fdt == SPT_BF16)
+            normalize_kernel<__nv_bfloat16><<<nblocks, 256, 0, st>>>(
+                w.A32, w.V, In, ld, R, w.colsq, (__nv_bfloat16 *)factors[n], lambda, last, w.inner);
+        else
+            normalize_kernel<__half><<<nblocks, 256, 0, st>>>(w.A32, w.V, In, ld, R, w.colsq,
+                                                              (__half *)factors[n], lambda, last, w.inner);
+        SPT_LAUNCH_CHECK("normalize_kernel");
+        s = gram_any(fdt, factors[n], In, ld, R, w.G + (size_t)n * R * R, st);
+        if (s) return s;
+    }
+    fit_kernel<<<1, 256, 0, st>>>(w.G, d, R, lambda, w.inner, t->xnorm2, fit_out);
+    SPT_LAUNCH_CHECK("fit_kernel");
+    return SPT_OK;
+}
+
+// CUDA-graph cache: one executable graph per argument set and tensor state.
+typedef std::tuple<spt_tensor, uint64_t, int, int, int, const void *, const void *, const void *,
+                   const void *, const void *, const void *, const void *, const void *, const void *,
+                   int>
+    GraphKey;
+std::mutex g_graph_mu;
+std::map<GraphKey, cudaGraphExec_t> g_graphs;
+
+}  // namespace
+
+void drop_graphs(spt_tensor t) {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end();) {
+        if (std::get<0>(it->first) == t) {
+            cudaGraphExecDestroy(it->second);
+            it = g_graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+}  // namespace spt
+
+using namespace spt;
+
+extern "C" {
+
+spt_status cp_als_workspace_size(spt_tensor t, int rank, int ld, size_t *bytes) {
+    if (!t || !bytes) return fail(SPT_EINVAL, "cp_als_workspace_size: NULL argument");
+    if (rank < 1 || rank > MAXR) return fail(SPT_EUNSUPPORTED, "cp_als_workspace_size: rank must be in [1, 128]");
+    if (ld < rank || ld % 8) return fail(SPT_EINVAL, "cp_als_workspace_size: bad ld");
+    *bytes = ws_layout(t, rank, ld, nullptr, nullptr);
+    return SPT_OK;
+}
+
+spt_status cp_als_step(spt_tensor t, void *const *factors, spt_dtype fdt, int rank, int ld,
+                       double *lambda, double *fit_out, void *workspace, size_t workspace_bytes,
+                       void *stream) {
+    if (!t || !factors || !lambda || !workspace) return fail(SPT_EINVAL, "cp_als_step: NULL argument");
+    if (!t->coalesced) return fail(SPT_ESTATE, "cp_als_step: the tensor must be created with SPT_COALESCE");
+    if (t->d > SPT_MAX_KERNEL_ORDER) return fail(SPT_EUNSUPPORTED, "cp_als_step: order > 5");
+    if (rank < 1 || rank > MAXR) return fail(SPT_EUNSUPPORTED, "cp_als_step: rank must be in [1, 128]");
+    if (fdt != SPT_F32 && fdt != SPT_BF16 && fdt != SPT_F16) return fail(SPT_EINVAL, "cp_als_step: bad dtype");
+    if (ld < rank || ld % 8) return fail(SPT_EINVAL, "cp_als_step: ld must be >= rank and a multiple of 8");
+    if ((uintptr_t)workspace & 255) return fail(SPT_EINVAL, "cp_als_step: workspace must be 256-byte aligned");
+    for (int m = 0; m < t->d; ++m)
+        if (!factors[m] || ((uintptr_t)factors[m] & 15))
+            return fail(SPT_EINVAL, "cp_als_step: a factor pointer is NULL or not 16-byte aligned");
+    Ws w;
+    const size_t need = ws_layout(t, rank, ld, &w, workspace);
+    if (workspace_bytes < need) return fail(SPT_EINVAL, "cp_als_step: workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+
+    const void *fp[SPT_MAX_KERNEL_ORDER] = {nullptr};
+    for (int m = 0; m < t->d; ++m) fp[m] = factors[m];
+    uint64_t state = 0;
+    for (int m = 0; m < t->d; ++m)
+        state = state * 4 + (t->sorted_buf[m] ? 2 : (t->perm[m] ? 1 : 0));
+    GraphKey key(t, state, (int)fdt, rank, ld, fp[0], fp[1], fp[2], fp[3], fp[4], lambda, fit_out,
+                 workspace, nullptr, t->d);
+    if (st != 0) {
+        cudaGraphExec_t exec = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(g_graph_mu);
+            auto it = g_graphs.find(key);
+            if (it != g_graphs.end()) exec = it->second;
+        }
+        if (!exec) {
+            cudaGraph_t graph = nullptr;
+            SPT_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            spt_status s = enqueue_step(t, factors, fdt, rank, ld, lambda, fit_out, w, st);
+            cudaError_t e = cudaStreamEndCapture(st, &graph);
+            if (s) { if (graph) cudaGraphDestroy(graph); return s; }
+            if (e != cudaSuccess) return cuda_fail(e, "cp_als_step: stream capture");
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "cp_als_step: graph instantiation");
+            std::lock_guard<std::mutex> lk(g_graph_mu);
+            g_graphs[key] = exec;
+        }
+        SPT_CUDA(cudaGraphLaunch(exec, st));
+        return SPT_OK;
+    }
+    return enqueue_step(t, factors, fdt, rank, ld, lambda, fit_out, w, st);
+}
+
+spt_status cp_als_status(void *workspace, void *stream) {
+    if (!workspace) return fail(SPT_EINVAL, "cp_als_status: NULL workspace");
+    int h = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    SPT_CUDA(cudaMemcpyAsync(&h, workspace, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SPT_CUDA(cudaStreamSynchronize(st));
+    if (h == SPT_DEV_SINGULAR)
+        return fail(SPT_ESINGULAR, "cp_als_step: a Gram-Hadamard matrix was not positive definite");
+    if (h) return fail(SPT_ECUDA, "cp_als_step: device status " + std::to_string(h));
+    return SPT_OK;
+}
+
+}  // extern "C"

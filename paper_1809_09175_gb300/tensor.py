@@ -1,0 +1,116 @@
+"""Torch-tensor convenience layer over the C ABI (argument marshalling only).
+
+``SparseTensor`` owns a library tensor handle; its methods pass torch device
+pointers and the current CUDA stream to the entry points of
+:mod:`.binding`.  No arithmetic of the method happens here.
+"""
+from __future__ import annotations
+
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+_TORCH_DT = {torch.float32: "f32", torch.bfloat16: "bf16", torch.float16: "f16"}
+
+
+def factor_ld(R: int) -> int:
+    """Row stride (elements) the library expects for rank R: a multiple of 8."""
+    return max(8, (R + 7) // 8 * 8)
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+class SparseTensor:
+    """A COO tensor resident on the current CUDA device.
+
+    ``idx`` is (d, P) int32 and ``vals`` (P,) float32, either numpy arrays
+    (host; copied by the library) or CUDA torch tensors (device; copied)."""
+
+    def __init__(self, idx, vals, dims: Sequence[int], coalesce: bool = False):
+        self.dims = [int(x) for x in dims]
+        d = len(self.dims)
+        flags = B.SPT_COALESCE if coalesce else 0
+        if isinstance(idx, torch.Tensor):
+            assert idx.is_cuda and idx.dtype == torch.int32 and vals.dtype == torch.float32
+            idx = idx.contiguous()
+            vals = vals.contiguous()
+            ptrs = [idx[m].data_ptr() for m in range(d)]
+            vptr = vals.data_ptr()
+            flags |= B.SPT_DEVICE_PTRS
+            keep = (idx, vals)
+        else:
+            idx = np.ascontiguousarray(idx, dtype=np.int32)
+            vals = np.ascontiguousarray(vals, dtype=np.float32)
+            ptrs = [idx[m].ctypes.data for m in range(d)]
+            vptr = vals.ctypes.data
+            keep = (idx, vals)
+        nnz = int(vals.shape[0])
+        self.handle = B.tensor_create_coo(d, self.dims, nnz, ptrs, vptr, flags, _stream())
+        del keep
+        _, _, self.nnz, fl = B.tensor_info(self.handle)
+        self.coalesced = bool(fl & B.SPT_COALESCE)
+        self.order = d
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.tensor_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_permutation(self, mode: int = -1, index_only: bool = False):
+        B.build_mode_permutation(self.handle, mode, B.SPT_PERM_INDEX_ONLY if index_only else 0,
+                                 _stream())
+
+    def permutation(self, mode: int) -> torch.Tensor:
+        out = torch.empty(self.nnz, dtype=torch.int32, device="cuda")
+        B.tensor_get_permutation(self.handle, mode, out.data_ptr(), _stream())
+        return out
+
+    def coo(self):
+        idx = torch.empty((self.order, self.nnz), dtype=torch.int32, device="cuda")
+        vals = torch.empty(self.nnz, dtype=torch.float32, device="cuda")
+        B.tensor_get_coo(self.handle, [idx[m].data_ptr() for m in range(self.order)],
+                         vals.data_ptr(), _stream())
+        return idx, vals
+
+    def norm2(self) -> float:
+        return B.tensor_norm2(self.handle)
+
+    def check(self):
+        B.tensor_check(self.handle, _stream())
+
+    def mttkrp(self, mode: int, factors: List[Optional[torch.Tensor]], rank: int,
+               lam: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+               sched: Optional[B.spt_schedule] = None) -> torch.Tensor:
+        f0 = next(f for m, f in enumerate(factors) if m != mode and f is not None) \
+            if self.order > 1 else None
+        ld = f0.shape[1] if f0 is not None else factor_ld(rank)
+        fdt = _TORCH_DT[f0.dtype] if f0 is not None else "f32"
+        if out is None:
+            out = torch.empty((self.dims[mode], ld), dtype=torch.float32, device="cuda")
+        ptrs = [0 if (m == mode or f is None) else f.data_ptr() for m, f in enumerate(factors)]
+        B.mttkrp(self.handle, mode, ptrs, fdt, rank, ld,
+                 lam.data_ptr() if lam is not None else 0, out.data_ptr(), sched, _stream())
+        return out
+
+    def cp_als_workspace(self, rank: int, ld: int) -> torch.Tensor:
+        nbytes = B.cp_als_workspace_size(self.handle, rank, ld)
+        return torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+
+    def cp_als_step(self, factors: List[torch.Tensor], rank: int, lam: torch.Tensor,
+                    fit: Optional[torch.Tensor], workspace: torch.Tensor):
+        ld = factors[0].shape[1]
+        fdt = _TORCH_DT[factors[0].dtype]
+        B.cp_als_step(self.handle, [f.data_ptr() for f in factors], fdt, rank, ld,
+                      lam.data_ptr(), fit.data_ptr() if fit is not None else 0,
+                      workspace.data_ptr(), workspace.numel(), _stream())

@@ -1,0 +1,70 @@
+"""The compiled library loads without a GPU and exports every entry point
+that include/spt.h declares; argument checks that need no device memory
+return their status codes."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported():
+    import paper_1809_09175_gb300 as P
+    L = P.binding.lib()
+    names = _declared()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_wraps_every_declared_symbol():
+    import paper_1809_09175_gb300 as P
+    missing = [n for n in _declared() if n not in P.binding.EXPORTED]
+    assert not missing, missing
+
+
+def test_argument_errors_without_device():
+    import paper_1809_09175_gb300 as P
+    with pytest.raises(P.SptError) as ei:
+        P.tensor_create_coo(0, [], 0, [], 0)
+    assert ei.value.status == P.SPT_EINVAL
+    with pytest.raises(P.SptError) as ei:
+        P.tensor_create_coo(3, [4, 0, 2], 0, [0, 0, 0], 0)
+    assert ei.value.status == P.SPT_EINVAL
+    with pytest.raises(P.SptError) as ei:
+        P.tensor_create_coo(2, [4, 4], 5, [0, 0], 0)
+    assert ei.value.status == P.SPT_EINVAL
+    assert "NULL" in P.spt_last_error()
+
+
+def test_paper_sizes_table_matches_golden():
+    """Tab. "sizes" (Sec. 4) as printed: vector_size and FBS for each R range."""
+    import paper_1809_09175_gb300 as P
+    rows = []
+    for line in open(os.path.join(ROOT, "tests", "golden", "paper_tab_sizes.txt")):
+        line = line.split("#")[0].strip()
+        if line:
+            rows.append([int(x) for x in line.split()])
+    assert len(rows) == 13
+    for lo, hi, vs, fbs in rows:
+        for R in sorted({lo, hi, (lo + hi) // 2}):
+            assert P.mttkrp_paper_sizes(R) == (vs, fbs), R
+    # the schedule built from the table covers FBS columns with 16-byte chunks
+    for R in (1, 16, 24, 48, 64, 96, 128, 200):
+        vs, fbs = P.mttkrp_paper_sizes(R)
+        for fdt, vec in (("f32", 4), ("bf16", 8)):
+            s = P.mttkrp_paper_schedule(R, fdt, "sorted")
+            cover = s.lanes_per_nnz * s.chunks * vec
+            assert cover >= fbs and s.nnz_per_group == 128 and s.warps_per_cta == 4
