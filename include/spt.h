@@ -141,6 +141,34 @@ spt_status build_mode_permutation(spt_tensor t, int mode, int flags, void *strea
 /* Copy perm_n (P int32) to a caller device buffer. SPT_ESTATE if not built. */
 spt_status tensor_get_permutation(spt_tensor t, int mode, int32_t *perm, void *stream);
 
+/* Largest n mode_permutation_noalloc accepts (bounded by its 32 MiB static
+ * scratch area: two key/position buffer pairs, the digit histogram and the
+ * scan sums). */
+#define SPT_NOALLOC_MAX_NNZ 1835008
+
+/* The mode permutation of build_mode_permutation, computed without allocating
+ * any device memory.  The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc/cudaFree at this point -- for
+ * example code living inside a fixed device-memory budget owned by another
+ * allocator, or code that must not incur the device-wide synchronisation of
+ * cudaFree -- and therefore cannot let the library allocate sort buffers.
+ *  keys   : device, n int32 mode coordinates (the tensor's l_{i,n}), each in
+ *           [0, dim); other values give an unspecified (but in-bounds) order.
+ *  n      : number of coordinates, 0 <= n <= SPT_NOALLOC_MAX_NNZ; larger n is
+ *           rejected with SPT_EINVAL before any work is queued.
+ *  dim    : the mode length I_n (sets the number of 8-bit radix passes).
+ *  perm   : device, n int32 output: positions in increasing key order, equal
+ *           keys in position order (the same result as perm_n).
+ * The sort works in one static device array that is part of the library and
+ * stays allocated on every GPU that has loaded it until the process exits.
+ * The first call on each device looks up that array's device address (with
+ * the device current), so make that first call before any stream capture.
+ * Every call uses the same array and leaves its last contents there; calls
+ * that overlap on the GPU (other streams or host threads) race on it, so the
+ * caller must order them.  Nothing is allocated or freed. */
+spt_status mode_permutation_noalloc(const int32_t *keys, int64_t n, int64_t dim, int32_t *perm,
+                                    void *stream);
+
 /* ---- MTTKRP (Sec. 2 eq. mttkrp; Figs. MTTKRP-A/B/C) -------------------- */
 
 /* Mode-n MTTKRP:  out(k, j) = lambda_j * sum_{i : l_in = k} x_i *

@@ -105,6 +105,8 @@ _try_sig("cp_als_workspace_size", _vp, C.c_int, C.c_int, C.POINTER(C.c_size_t))
 _try_sig("cp_als_step", _vp, C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _vp, _vp, _vp,
          C.c_size_t, _vp)
 _try_sig("cp_als_status", _vp, _vp)
+_try_sig("mode_permutation_noalloc", _vp, C.c_int64, C.c_int64, _vp, _vp)
+SPT_NOALLOC_MAX_NNZ = 1835008
 
 
 def lib():
@@ -226,3 +228,9 @@ def cp_als_step(t: int, factor_ptrs: Sequence[int], fdt, rank: int, ld: int, lam
 
 def cp_als_status(workspace_ptr: int, stream: int = 0):
     _chk(_L.cp_als_status(workspace_ptr, stream or None))
+
+
+def mode_permutation_noalloc(keys_ptr: int, n: int, dim: int, perm_ptr: int, stream: int = 0):
+    """Mode permutation computed in the library's static scratch area, for
+    callers that cannot allocate device memory (see include/spt.h)."""
+    _chk(_L.mode_permutation_noalloc(keys_ptr or None, n, dim, perm_ptr or None, stream or None))

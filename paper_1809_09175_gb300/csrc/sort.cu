@@ -8,6 +8,8 @@
 // scatter in which each warp ranks its items with __match_any_sync and the
 // warps of a tile are ordered by a shared-memory prefix.  Tiles, warps,
 // rounds and lanes all follow position order, so equal keys keep their order.
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -506,4 +508,119 @@ spt_status compute_norm2(spt_tensor t, cudaStream_t st) {
     return SPT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free mode permutation.
+//
+// Some callers cannot allocate device memory when they need a permutation:
+// code running inside someone else's fixed memory budget (a serving process
+// whose pool owns every byte of the GPU), code that must not trigger the
+// device-wide synchronisation cudaFree implies, or a driver that sets up all
+// memory once and then only launches work.  For them this entry point sorts
+// with a scratch area that is part of the library image itself: a static
+// device array, created when the library is loaded on a GPU and kept until
+// the process exits.  The caller passes the coordinates in and receives the
+// permutation; nothing is allocated or freed on the way.
+//
+// The area holds the two ping-pong key/position buffers of the radix sort,
+// the digit histogram and the scan's block sums, which bounds n to
+// SPT_NOALLOC_MAX_NNZ.  Every pass overwrites what the next one reads, so
+// nothing in the area has to start at zero.  All calls in the process share
+// the one area: calls whose work overlaps on the GPU (other streams, other
+// host threads) race on it and must be ordered by the caller.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;  // 32 MiB per GPU
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the scratch area on the current device.  The first call
+// on a device looks it up (with that device current); later calls reuse it.
+spt_status noalloc_scratch(void **out) {
+    int dev = 0;
+    SPT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(SPT_EUNSUPPORTED, "device index >= 64");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SPT_OK;
+}
+
+struct Carve {
+    char *p;
+    size_t left;
+    template <typename T> T *take(size_t count) {
+        const size_t bytes = (count * sizeof(T) + 255) / 256 * 256;
+        if (bytes > left) return nullptr;
+        T *r = reinterpret_cast<T *>(p);
+        p += bytes;
+        left -= bytes;
+        return r;
+    }
+};
+
+// In-place exclusive scan with block sums carved from the static area.
+spt_status scan_inplace_carved(int32_t *data, int64_t n, Carve &cv, cudaStream_t st) {
+    if (n <= 0) return SPT_OK;
+    const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    int32_t *sums = cv.take<int32_t>(nb);
+    if (!sums) return fail(SPT_EINVAL, "noalloc scratch exhausted in scan");
+    scan_block_kernel<<<(unsigned)nb, SCAN_T, 0, st>>>(data, data, n, sums);
+    SPT_LAUNCH_CHECK("scan_block_kernel");
+    if (nb > 1) {
+        spt_status s = scan_inplace_carved(sums, nb, cv, st);
+        if (s) return s;
+        scan_add_kernel<<<(unsigned)nb, SCAN_T, 0, st>>>(data, n, sums);
+        SPT_LAUNCH_CHECK("scan_add_kernel");
+    }
+    return SPT_OK;
+}
+}  // namespace
+
 }  // namespace spt
+
+using namespace spt;
+
+extern "C" spt_status mode_permutation_noalloc(const int32_t *keys, int64_t n, int64_t dim,
+                                               int32_t *perm, void *stream) {
+    if (n < 0 || n > SPT_NOALLOC_MAX_NNZ)
+        return fail(SPT_EINVAL, "mode_permutation_noalloc: n must be in [0, " +
+                                    std::to_string((long long)SPT_NOALLOC_MAX_NNZ) +
+                                    "] (the size of the static scratch area)");
+    if (dim < 1 || dim > INT32_MAX) return fail(SPT_EINVAL, "mode_permutation_noalloc: dim must be in [1, 2^31-1]");
+    if (n == 0) return SPT_OK;
+    if (!keys || !perm) return fail(SPT_EINVAL, "mode_permutation_noalloc: NULL keys or perm");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *base = nullptr;
+    spt_status s = noalloc_scratch(&base);
+    if (s) return s;
+    Carve cv{reinterpret_cast<char *>(base), NOALLOC_SCRATCH_BYTES};
+    const int bits = bit_width_u32((uint64_t)(dim - 1));
+    const int passes = std::max(1, (bits + 7) / 8);
+    const int64_t ntiles = (n + RTILE - 1) / RTILE;
+    uint32_t *kb[2] = {cv.take<uint32_t>(n), cv.take<uint32_t>(n)};
+    int32_t *vb[2] = {cv.take<int32_t>(n), cv.take<int32_t>(n)};
+    int32_t *hist = cv.take<int32_t>(256 * ntiles);
+    if (!kb[0] || !kb[1] || !vb[0] || !vb[1] || !hist)
+        return fail(SPT_EINVAL, "mode_permutation_noalloc: n too large for the static scratch area");
+    for (int p = 0; p < passes; ++p) {
+        const uint32_t *ik = p == 0 ? reinterpret_cast<const uint32_t *>(keys) : kb[(p - 1) & 1];
+        const int32_t *iv = p == 0 ? nullptr : vb[(p - 1) & 1];
+        int32_t *ov = p == passes - 1 ? perm : vb[p & 1];
+        radix_hist_kernel<<<(unsigned)ntiles, RT, 0, st>>>(ik, n, 8 * p, hist, ntiles);
+        SPT_LAUNCH_CHECK("radix_hist_kernel");
+        Carve scan_cv = cv;  // the scan's block sums reuse the same tail every pass
+        s = scan_inplace_carved(hist, 256 * ntiles, scan_cv, st);
+        if (s) return s;
+        radix_scatter_kernel<<<(unsigned)ntiles, RT, 0, st>>>(ik, iv, n, 8 * p, hist, ntiles,
+                                                             kb[p & 1], ov);
+        SPT_LAUNCH_CHECK("radix_scatter_kernel");
+    }
+    return SPT_OK;
+}
