@@ -1,12 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the sparse MTTKRP / CP-ALS hot path on GB300.
 
-One *step* is one pass of the whole hot path over the workload: one CP-ALS
-iteration (every mode: MTTKRP, Gram-Hadamard FP64 Cholesky solve, column
-normalisation, then the fit) when the library has it, else the MTTKRP of
-every mode.  The default workload is the 3-way power-law tensor
-1,000,000 x 500,000 x 200,000 with 1e8 nonzeros (Zipf s=1.2 per mode),
-rank 16, fp32 N(0,1) factors.
+One timed *step* is the MTTKRP of every mode of the workload (one kernel
+launch per mode, the permuted traversal over mode-sorted copies by default).
+The default workload is the 3-way power-law tensor 1,000,000 x 500,000 x
+200,000 with 1e8 nonzeros (Zipf s=1.2 per mode, duplicates kept), rank 16,
+fp32 N(0,1) factors.  After the timed region the line also reports the other
+scatter strategies and bf16 factors on the same tensor, sampled-row errors
+against the FP64 oracle, and CP-ALS iterations (captured CUDA graph) on the
+coalesced tensor.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle instead, on a bounded sample of the same workload.
@@ -44,7 +46,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=4_000_000,
                     help="nonzeros of the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--step-kind", default="auto", choices=["auto", "mttkrp", "cpals"])
+    ap.add_argument("--quick", action="store_true", help="skip the variants / CP-ALS extras")
     return ap.parse_args()
 
 
@@ -182,6 +184,21 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm
+def _dev_factor(torch, f, dtype):
+    if dtype == "f32":
+        return torch.from_numpy(f).cuda()
+    return torch.from_numpy(f.view(np.int16)).cuda().view(
+        torch.bfloat16 if dtype == "bf16" else torch.float16)
+
+
+def sampled_rows(w, idx, n, R, count=24, seed=0):
+    """Hottest rows of mode n plus uniformly drawn ones (oracle-checkable)."""
+    cnt = np.bincount(idx[n], minlength=w.dims[n])
+    hot = np.argsort(cnt)[::-1][: count // 2]
+    rnd = np.random.default_rng(seed).integers(0, w.dims[n], count - hot.shape[0])
+    return np.unique(np.concatenate([hot, rnd])).astype(np.int32)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -197,7 +214,7 @@ def run_ours(args):
     import synth
 
     w = synth.workload(args.workload, args.scale)
-    if world > 1:  # independent problem per rank (weak scaling)
+    if world > 1:  # an independent problem per rank (weak scaling, no collective)
         w = synth.Workload(w.name, w.dims, w.nnz, w.s, w.R, w.factor_dist, w.seed + rank,
                            w.factor_dtype)
     dtype = args.dtype or w.factor_dtype
@@ -209,47 +226,39 @@ def run_ours(args):
     facs_np = w.factors(R, dtype)
 
     stream = torch.cuda.current_stream()
+    sid = stream.cuda_stream
     t_ing = time.perf_counter()
     T = P.SparseTensor(idx, vals, w.dims)
+    torch.cuda.synchronize()
+    t_perm = time.perf_counter()
     T.build_permutation(-1, index_only=(args.scatter == "perm"))
     torch.cuda.synchronize()
-    ingest_s = time.perf_counter() - t_ing
+    t_done = time.perf_counter()
+    ingest_s, perm_s = t_perm - t_ing, t_done - t_perm
 
-    def dev_factor(f):
-        if dtype == "f32":
-            return torch.from_numpy(f).cuda()
-        return torch.from_numpy(f.view(np.int16)).cuda().view(
-            torch.bfloat16 if dtype == "bf16" else torch.float16)
-
-    facs = [dev_factor(f) for f in facs_np]
+    facs = [_dev_factor(torch, f, dtype) for f in facs_np]
     outs = [torch.empty((I, ld), dtype=torch.float32, device="cuda") for I in w.dims]
-    scheds = []
-    for n in range(d):
-        s = P.mttkrp_default_schedule(T.handle, n, dtype, R)
-        s.scatter = P.SCATTERS[args.scatter]
-        scheds.append(s)
 
-    has_cpals = hasattr(P.binding.lib(), "cp_als_step")
-    kind = args.step_kind
-    if kind == "auto":
-        kind = "cpals" if has_cpals else "mttkrp"
+    def sched_for(n, scatter, fdt):
+        s = P.mttkrp_default_schedule(T.handle, n, fdt, R)
+        s.scatter = P.SCATTERS[scatter]
+        return s
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(d)]
-    kern_ms = []
+    scheds = [sched_for(n, args.scatter, dtype) for n in range(d)]
+    # one event pair per launch of the timed region (steps x modes)
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(d)] for _ in range(args.steps)]
 
-    def mttkrp_step(record):
+    def step(k=None):
         for n in range(d):
-            if record:
-                ev[n][0].record(stream)
+            if k is not None:
+                ev[k][n][0].record(stream)
             T.mttkrp(n, facs, R, out=outs[n], sched=scheds[n])
-            if record:
-                ev[n][1].record(stream)
-
-    step = mttkrp_step
-    launches_per_step = d
+            if k is not None:
+                ev[k][n][1].record(stream)
 
     for _ in range(args.warmup):
-        step(False)
+        step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -260,12 +269,8 @@ def run_ours(args):
     t1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     t0.record(stream)
-    per_mode = [0.0] * d
-    for _ in range(args.steps):
-        step(True)
-        torch.cuda.synchronize()
-        for n in range(d):
-            per_mode[n] += ev[n][0].elapsed_time(ev[n][1])
+    for k in range(args.steps):
+        step(k)
     t1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -277,45 +282,44 @@ def run_ours(args):
         total_ms = float(tt.item())
         dist.barrier()
     ms_step = total_ms / args.steps
-    units = w.nnz * R * d  # nonzeros x rank per mode, every mode
+    units = w.nnz * R * d
     value = units * world / (ms_step / 1e3)
+    mode_ms = [sum(ev[k][n][0].elapsed_time(ev[k][n][1]) for k in range(args.steps)) / args.steps
+               for n in range(d)]
 
-    # roofline of the dominant kernel (the MTTKRP launch), per mode averaged
-    stats = []
     hbm_peak, peak_kind = measured_peaks()
-    alg = 0.0
-    comp = 0.0
-    for n in range(d):
-        W = w.dims[n]
-        alg += algorithmic_bytes(args.scatter, w.nnz, d, R, s_f, w.dims[n], W)
-        comp += compulsory_bytes(w.nnz, d, w.dims, n, R, s_f)
-    mode_ms = [x / args.steps for x in per_mode]
+    # W (rows written) is bounded by I_n; the bound is used
+    alg = sum(algorithmic_bytes(args.scatter, w.nnz, d, R, s_f, w.dims[n], w.dims[n])
+              for n in range(d))
+    comp = sum(compulsory_bytes(w.nnz, d, w.dims, n, R, s_f) for n in range(d))
     launch_ms = sum(mode_ms) / d
     achieved = (alg / d) / (launch_ms / 1e3) / 1e9
     comp_gbs = (comp / d) / (launch_ms / 1e3) / 1e9
 
-    # end to end through the public API: factors H2D from pinned memory, the
-    # step, results D2H, every step
-    e2e = None
-    if rank == 0 or world > 1:
-        pin_f = [torch.from_numpy(f.view(np.int16) if dtype != "f32" else f).pin_memory() for f in facs_np]
-        pin_o = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
-        h2d = sum(p.numel() * p.element_size() for p in pin_f)
-        d2h = sum(p.numel() * p.element_size() for p in pin_o)
+    # end to end through the public API: the factors H2D from pinned host
+    # memory, every mode's MTTKRP, every output D2H, each step
+    pin_f = [torch.from_numpy(f.view(np.int16) if dtype != "f32" else f).pin_memory() for f in facs_np]
+    pin_o = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+    h2d = sum(p.numel() * p.element_size() for p in pin_f)
+    d2h = sum(p.numel() * p.element_size() for p in pin_o)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        for f, p in zip(facs, pin_f):
+            f.view(p.dtype).copy_(p, non_blocking=True)
+        step()
+        for o, p in zip(outs, pin_o):
+            p.copy_(o, non_blocking=True)
         torch.cuda.synchronize()
-        e0 = time.perf_counter()
-        for _ in range(args.steps):
-            for f, p in zip(facs, pin_f):
-                f.view(p.dtype).copy_(p, non_blocking=True)
-            step(False)
-            for o, p in zip(outs, pin_o):
-                p.copy_(o, non_blocking=True)
-            torch.cuda.synchronize()
-        e_s = (time.perf_counter() - e0) / args.steps
-        e2e = {"value": units / e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+    e_s = (time.perf_counter() - e0) / args.steps
+    e2e = {"value": units / e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    extra = {}
+    if rank == 0 and not args.quick:
+        extra = measure_extras(args, P, torch, w, T, idx, vals, facs_np, dtype, R, d, ld, outs,
+                               sched_for, mode_ms)
     if rank != 0:
+        T.close()
         if world > 1:
             dist.destroy_process_group()
         return
@@ -325,28 +329,101 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32-accumulate/" + dtype + "-factors",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": w.name, "dims": w.dims, "nnz": w.nnz, "zipf_s": w.s, "R": R,
                    "factors": dtype, "factor_dist": w.factor_dist, "scatter": args.scatter,
-                   "step": kind, "l2": "inputs larger than L2 (COO stream "
-                   f"{w.nnz * 4 * (d + 1) / 1e9:.1f} GB per mode)"},
+                   "step": "MTTKRP of every mode (one launch per mode)",
+                   "l2": "inputs larger than L2 (COO stream "
+                   f"{w.nnz * 4 * (d + 1) / 1e9:.1f} GB per mode pass)"},
         "per_mode_ms": mode_ms,
         "per_mode_nnzR_per_s": [w.nnz * R / (m / 1e3) for m in mode_ms],
         "roofline": {"bound": "hbm", "kernel": "mttkrp_kernel", "achieved": achieved,
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                      "peak_kind": peak_kind, "traffic": None,
                      "compulsory_GBps": comp_gbs, "compulsory_frac": comp_gbs / hbm_peak},
-        "gpu_launches": launches_per_step * args.steps,
-        "ingest_s": ingest_s,
+        "gpu_launches": d * args.steps,
+        "ingest_s": ingest_s, "permutation_s": perm_s,
         "clocks": clk,
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
     T.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def measure_extras(args, P, torch, w, T, idx, vals, facs_np, dtype, R, d, ld, outs, sched_for,
+                   mode_ms):
+    """Variants (scatter x factor precision), CP-ALS iterations and sampled
+    errors against the oracle -- reported beside the headline number."""
+    import oracle
+    stream = torch.cuda.current_stream()
+    out = {}
+    # ---- scatter x precision, MTTKRP only, ms per mode
+    var = {}
+    for fdt in ["f32", "bf16"]:
+        fnp = w.factors(R, fdt)
+        fd = [_dev_factor(torch, f, fdt) for f in fnp]
+        for sc in (["sorted"] if args.scatter != "perm" else []) + ["perm", "atomic"]:
+            ms = []
+            for n in range(d):
+                s = sched_for(n, sc, fdt)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                T.mttkrp(n, fd, R, out=outs[n], sched=s)
+                e0.record(stream)
+                for _ in range(3):
+                    T.mttkrp(n, fd, R, out=outs[n], sched=s)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1) / 3)
+            # sampled-row error against the oracle (same stored factor values)
+            errs = []
+            A64 = [oracle.as_f64(f, fdt)[:, :R].copy() for f in fnp]
+            if sc == "sorted" or sc == "atomic":
+                for n in range(d):
+                    rows = sampled_rows(w, idx, n, R)
+                    T.mttkrp(n, fd, R, out=outs[n], sched=sched_for(n, sc, fdt))
+                    got = outs[n][torch.from_numpy(rows).long().cuda(), :R].double().cpu().numpy()
+                    ref = oracle.mttkrp_rows(idx, vals, w.dims, A64, n, R, rows)
+                    errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+            var[f"{sc}/{fdt}"] = {"ms_per_mode": ms,
+                                  "nnzR_per_s": w.nnz * R * d / (sum(ms) / 1e3),
+                                  "rel_err_sampled_rows": errs or None}
+        del fd
+    out["variants"] = var
+    # ---- CP-ALS iterations on the coalesced tensor (duplicates summed)
+    Tc = P.SparseTensor(idx, vals, w.dims, coalesce=True)
+    t0 = time.perf_counter()
+    Tc.build_permutation()
+    torch.cuda.synchronize()
+    sort_s = time.perf_counter() - t0
+    fc = [_dev_factor(torch, f, dtype) for f in facs_np]
+    lam = torch.zeros(R, dtype=torch.float64, device="cuda")
+    fit = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ws = Tc.cp_als_workspace(R, ld)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            Tc.cp_als_step(fc, R, lam, fit, ws)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        iters = 5
+        for _ in range(iters):
+            Tc.cp_als_step(fc, R, lam, fit, ws)
+        e1.record(side)
+    torch.cuda.synchronize()
+    it_ms = e0.elapsed_time(e1) / iters
+    out["cp_als"] = {"nnz_coalesced": Tc.nnz, "ms_per_iter": it_ms, "iter_per_s": 1e3 / it_ms,
+                     "fit": float(fit.item()), "graph": True,
+                     "permutation_build_s": sort_s,
+                     "permutation_cost_in_iterations": sort_s * 1e3 / it_ms}
+    Tc.close()
+    return out
 
 
 if __name__ == "__main__":

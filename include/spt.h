@@ -18,7 +18,8 @@
  *  - Coordinates are 0-based int32; P < 2^31; order d in [1, 8] for storage,
  *    d in [1, 5] for the MTTKRP kernels.
  *  - Factor matrices are row-major I_m x ld with ld >= rank, ld a multiple
- *    of 8 elements, base pointer 16-byte aligned.  Element type spt_dtype.
+ *    of 8 elements (ld <= 2^28), base pointer 16-byte aligned.  Element type
+ *    spt_dtype.
  *  - Asynchronous CUDA errors surface as SPT_ECUDA at a later call.
  */
 #ifndef SPT_H
@@ -65,8 +66,9 @@ typedef enum {
 /* A launch schedule of the MTTKRP kernel.
  *  lanes_per_nnz : 1,2,4,8,16,32 lanes share one nonzero (the paper's
  *                  vector_size, Tab. "sizes"); groups per warp = 32/lanes.
- *  chunks        : 1 or 2 sixteen-byte column chunks per lane; the rank
- *                  block (the paper's FBS) = lanes * chunks * (16 / elem bytes).
+ *  chunks        : 1 or 2 four-column chunks per lane (one 16-byte load for
+ *                  fp32, 8-byte for 16-bit factors); the rank block (the
+ *                  paper's FBS) = lanes * chunks * 4 columns.
  *  nnz_per_group : nonzeros one lane group walks in order (the paper's
  *                  NZPTM); adjusted by the library for bank-conflict-free
  *                  staging.

@@ -246,6 +246,7 @@ spt_status mttkrp(spt_tensor t, int mode, const void *const *factors, spt_dtype 
     if (fdt != SPT_F32 && fdt != SPT_BF16 && fdt != SPT_F16) return fail(SPT_EINVAL, "mttkrp: bad dtype");
     if (rank < 1) return fail(SPT_EINVAL, "mttkrp: rank must be >= 1");
     if (ld < rank || ld % 8) return fail(SPT_EINVAL, "mttkrp: ld must be >= rank and a multiple of 8");
+    if (ld > (1 << 28)) return fail(SPT_EUNSUPPORTED, "mttkrp: ld above 2^28 elements");
     if (!out || ((uintptr_t)out & 15)) return fail(SPT_EINVAL, "mttkrp: out NULL or not 16-byte aligned");
     if (t->d > 1 && !factors) return fail(SPT_EINVAL, "mttkrp: factors is NULL");
     for (int m = 0; m < t->d; ++m) {
@@ -298,7 +299,8 @@ spt_status mttkrp_paper_schedule(int rank, spt_dtype fdt, int scatter, spt_sched
     int vs = 0, fbs = 0;
     spt_status s = mttkrp_paper_sizes(rank, &vs, &fbs);
     if (s) return s;
-    const int vec = 16 / elem_bytes(fdt);
+    const int vec = 4;  // columns per lane chunk
+    (void)fdt;
     int need = (fbs + vec - 1) / vec;
     int lanes = 1;
     while (lanes < need && lanes < 32) lanes <<= 1;

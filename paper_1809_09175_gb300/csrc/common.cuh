@@ -42,11 +42,11 @@ struct spt_tensor_s {
     void *coo_buf = nullptr;
     int32_t *idx[SPT_MAX_ORDER] = {nullptr};
     float *vals = nullptr;
-    // per mode: permutation and optional mode-sorted copy (d index arrays + values)
+    // per mode: permutation and optional mode-sorted copy, stored as packed
+    // records {row, other coordinates in increasing mode order, value bits}
+    // of record_words(d) int32 words each
     int32_t *perm[SPT_MAX_ORDER] = {nullptr};
     void *sorted_buf[SPT_MAX_ORDER] = {nullptr};
-    int32_t *sidx[SPT_MAX_ORDER][SPT_MAX_ORDER] = {{nullptr}};
-    float *svals[SPT_MAX_ORDER] = {nullptr};
     ModeStats stats[SPT_MAX_ORDER];
     int *dev_err = nullptr;  // device status word for kernels of this tensor
 };
@@ -132,31 +132,44 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
-// Element traits: 16 bytes of factor row = VEC elements, widened to float.
+// Element traits: every lane works on chunks of VEC = 4 consecutive factor
+// columns, loaded as one vector (16 bytes for fp32, 8 bytes for 16-bit
+// types) and widened to float.
 template <typename T> struct Elem;
 template <> struct Elem<float> {
     static constexpr int VEC = 4;
     static constexpr int BYTES = 4;
-    __device__ __forceinline__ static void widen(const uint4 &r, float *o) {
+    typedef uint4 Raw;
+    __device__ __forceinline__ static Raw load(const void *p) {
+        return __ldg(reinterpret_cast<const uint4 *>(p));
+    }
+    __device__ __forceinline__ static void widen(const Raw &r, float *o) {
         o[0] = __uint_as_float(r.x); o[1] = __uint_as_float(r.y);
         o[2] = __uint_as_float(r.z); o[3] = __uint_as_float(r.w);
     }
 };
 template <> struct Elem<__nv_bfloat16> {
-    static constexpr int VEC = 8;
+    static constexpr int VEC = 4;
     static constexpr int BYTES = 2;
-    __device__ __forceinline__ static void widen(const uint4 &r, float *o) {
+    typedef uint2 Raw;
+    __device__ __forceinline__ static Raw load(const void *p) {
+        return __ldg(reinterpret_cast<const uint2 *>(p));
+    }
+    __device__ __forceinline__ static void widen(const Raw &r, float *o) {
         o[0] = bf16_lo(r.x); o[1] = bf16_hi(r.x); o[2] = bf16_lo(r.y); o[3] = bf16_hi(r.y);
-        o[4] = bf16_lo(r.z); o[5] = bf16_hi(r.z); o[6] = bf16_lo(r.w); o[7] = bf16_hi(r.w);
     }
 };
 template <> struct Elem<__half> {
-    static constexpr int VEC = 8;
+    static constexpr int VEC = 4;
     static constexpr int BYTES = 2;
-    __device__ __forceinline__ static void widen(const uint4 &r, float *o) {
-        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+    typedef uint2 Raw;
+    __device__ __forceinline__ static Raw load(const void *p) {
+        return __ldg(reinterpret_cast<const uint2 *>(p));
+    }
+    __device__ __forceinline__ static void widen(const Raw &r, float *o) {
+        const uint32_t w[2] = {r.x, r.y};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 2; ++q) {
             __half2 h = *reinterpret_cast<const __half2 *>(&w[q]);
             float2 f = __half22float2(h);
             o[2 * q] = f.x;

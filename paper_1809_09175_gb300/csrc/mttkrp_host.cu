@@ -24,7 +24,7 @@ bool pow2_in(int x, int lo, int hi) { return x >= lo && x <= hi && (x & (x - 1))
 // G = 2, S a multiple of 4 for G = 1.
 int adjust_S(int want, int G) {
     int S = std::max(1, want);
-    if (G >= 4) return S | 1;
+    if (G >= 4) return (S & 1) ? S : S - 1;  // round down to odd
     if (G == 2) return std::max(2, (S & ~3) | 2);
     return std::max(4, (S + 3) & ~3);
 }
@@ -46,14 +46,18 @@ spt_schedule default_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank) {
     spt_schedule s{};
     s.scatter = t->sorted_buf[mode] ? SPT_SCATTER_SORTED
                                     : (t->perm[mode] ? SPT_SCATTER_PERM : SPT_SCATTER_ATOMIC);
-    const int vec = 16 / elem_bytes(fdt);
+    const int vec = 4;  // columns per lane chunk
     const int need = (rank + vec - 1) / vec;
     int lanes = 1;
     while (lanes < need && lanes < 32) lanes <<= 1;
     s.lanes_per_nnz = lanes;
     s.chunks = need > 32 ? 2 : 1;
-    // about 256 nonzeros per warp chunk, whatever the number of groups
-    s.nnz_per_group = std::max(4, std::min(64, 256 / (32 / lanes)));
+    // staging of about 7 KB per warp (two stages of the d+1 arrays), so four
+    // 8-warp CTAs fit an SM's shared memory; at most 256 nonzeros per chunk
+    const int narr = s.scatter == SPT_SCATTER_PERM ? 1
+                     : (s.scatter == SPT_SCATTER_SORTED ? record_words(t->d) : t->d + 1);
+    const int npw = std::min(256, 896 / narr);
+    s.nnz_per_group = std::max(4, npw / (32 / lanes));
     s.warps_per_cta = 8;
     s.ctas_per_sm = 0;
     return s;
@@ -79,8 +83,7 @@ spt_status check_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank, const
 spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt,
                          int rank, int ld, const float *lambda, float *out,
                          const spt_schedule &s, cudaStream_t st) {
-    const int eb = elem_bytes(fdt);
-    const int vec = 16 / eb;
+    const int vec = 4;  // columns per lane chunk
     const int L = s.lanes_per_nnz, C = s.chunks;
     const int G = 32 / L;
     const int rb_cols = L * C * vec;
@@ -94,13 +97,14 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
     const int kmode = s.scatter == SPT_SCATTER_ATOMIC ? M_ATOMIC
                       : (s.scatter == SPT_SCATTER_SORTED ? M_SORTED : M_PERM);
     MttkrpParams p{};
-    p.rows = kmode == M_SORTED ? t->sidx[mode][mode] : t->idx[mode];
-    p.vals = kmode == M_SORTED ? t->svals[mode] : t->vals;
+    p.rows = t->idx[mode];
+    p.vals = t->vals;
     p.perm = t->perm[mode];
+    p.rec = reinterpret_cast<const int32_t *>(t->sorted_buf[mode]);
     int q = 0;
     for (int m = 0; m < t->d; ++m) {
         if (m == mode) continue;
-        p.oidx[q] = kmode == M_SORTED ? t->sidx[mode][m] : t->idx[m];
+        p.oidx[q] = t->idx[m];
         p.fac[q] = factors[m];
         ++q;
     }
@@ -118,8 +122,8 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
     p.nchunks = (t->nnz + npw - 1) / npw;
     p.err = t->dev_err;
 
-    const int narr = kmode == M_PERM ? 1 : D1 + 2;
-    const size_t smem = 16 * (size_t)wpc + (size_t)wpc * 2 * narr * npw * 4;
+    const int wpe = kmode == M_PERM ? 1 : (kmode == M_SORTED ? record_words(t->d) : D1 + 2);
+    const size_t smem = 16 * (size_t)wpc + (size_t)wpc * 2 * wpe * npw * 4;
     if (smem > 227 * 1024)
         return fail(SPT_EINVAL, "schedule: staging buffers exceed 227 KB of shared memory "
                                 "(lower warps_per_cta or nnz_per_group)");

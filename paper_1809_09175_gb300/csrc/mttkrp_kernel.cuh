@@ -6,29 +6,35 @@
 // Sec. 3 Tab. "Levels of Parallelism"):
 //  * A warp owns a chunk of `npw` consecutive nonzeros of the traversal order
 //    (persistent grid, chunks dealt round-robin to warps).  The chunk's
-//    coordinates and values (or, for the permuted traversal, its permutation
-//    entries) are staged into the warp's shared memory with 1-D bulk copies
+//    nonzeros are staged into the warp's shared memory with 1-D bulk copies
 //    (cp.async.bulk, mbarrier completion), double buffered, so the next chunk
 //    streams in while this one is computed.
 //  * The warp is split into G = 32/L groups of L lanes.  Group g walks the
 //    nonzeros [g*S, g*S+S) of the chunk in order (the paper's NZPTM block,
-//    Fig. MTTKRP-C); lane l of the group owns 16-byte column chunks of the
-//    rank block (the paper's vector lanes over j, Fig. MTTKRP-B), loading
-//    the d-1 factor rows with coalesced 16-byte loads and keeping the
-//    running row sum in registers (the paper's TinyVec).
+//    Fig. MTTKRP-C); lane l of the group owns 4-column chunks of the rank
+//    block (the paper's vector lanes over j, Fig. MTTKRP-B), loading the d-1
+//    factor rows with coalesced vector loads (16 bytes per chunk for fp32,
+//    8 for 16-bit factors) and keeping the running row sum in registers (the
+//    paper's TinyVec).
 //  * Scatter:
-//      M_ATOMIC  storage order; a group's running sum is added atomically
-//                (16-byte vector red) whenever its row changes (Fig. MTTKRP-B
-//                with merging of equal consecutive rows).
-//      M_SORTED  nonzeros in mode-n order from a mode-sorted copy; M_PERM
-//                walks storage through the permutation (Fig. MTTKRP-C).  A
-//                group writes a finished row with a plain store; the first
-//                and last run of every group are combined across the warp
-//                with shuffles (a segmented reduction over the groups), and
-//                only the chunk's first and last row are added atomically,
-//                because only those rows can be shared with other warps.
+//      M_ATOMIC  storage order (coordinate arrays staged one by one); a
+//                group's running sum is added atomically (16-byte vector red)
+//                whenever its row changes (Fig. MTTKRP-B with merging of
+//                equal consecutive rows).
+//      M_SORTED  mode-n order from the mode-sorted copy, whose nonzeros are
+//                packed records {row, other coordinates, value} (one bulk copy
+//                and one vector shared load per nonzero);
+//      M_PERM    storage order walked through the permutation (Fig. MTTKRP-C):
+//                the permutation is staged, coordinates and values gathered.
+//                For both, a group writes a finished row with a plain store;
+//                the first and last run of every group are combined across
+//                the warp with shuffles (a segmented reduction over the
+//                groups), and only the chunk's first and last row are added
+//                atomically, because only those rows can be shared with other
+//                warps.
 //  * Columns: rank block rb covers columns [rb*L*C*VEC, ...); lane l's chunk
-//    c starts at column rb*L*C*VEC + (c*L + l)*VEC.  Columns >= R contribute 0.
+//    c starts at column rb*L*C*VEC + (c*L + l)*VEC.  Columns >= R are
+//    computed from the factors' padding and written as zeros.
 #pragma once
 #include "common.cuh"
 
@@ -36,13 +42,20 @@ namespace spt {
 
 enum MttkrpMode { M_ATOMIC = 0, M_SORTED = 1, M_PERM = 2 };
 
+// Words of one packed record of the mode-sorted copy: {row, d-1 other
+// coordinates, value} = d+1 words, padded to 2, 4 or 6 for vector loads.
+__host__ __device__ constexpr int record_words(int d) {
+    return d + 1 <= 2 ? 2 : (d + 1 <= 4 ? 4 : (d + 1 <= 6 ? 6 : ((d + 2) & ~1)));
+}
+
 struct MttkrpParams {
-    const int32_t *rows;     // mode-n coordinate, traversal order (M_PERM: storage order)
-    const int32_t *oidx[4];  // coordinates of the other modes (same order as rows)
-    const float *vals;       // values (same order as rows)
+    const int32_t *rows;     // M_ATOMIC / M_PERM: mode-n coordinates, storage order
+    const int32_t *oidx[4];  // M_ATOMIC / M_PERM: coordinates of the other modes
+    const float *vals;       // M_ATOMIC / M_PERM: values
     const int32_t *perm;     // M_PERM: traversal position -> storage position
+    const int32_t *rec;      // M_SORTED: packed records in mode-n order
     const void *fac[4];      // factor matrices of the other modes
-    int64_t fld;             // factor row stride (elements)
+    int fld;                 // factor row stride (elements)
     const float *lambda;     // nullable
     float *out;              // I_n x old, zeroed before launch
     int64_t old;
@@ -65,15 +78,22 @@ __device__ __forceinline__ void red_add4(float *dst, const float *v) {
     atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(v[0], v[1], v[2], v[3]));
 }
 
-template <int U_> struct Unroll { static constexpr int U = U_; };
+// Register cap: small column blocks fit two 512-thread CTAs (<= 64 registers).
+template <typename FT, int C> struct MinBlocks {
+    static constexpr int value = (Elem<FT>::VEC * C <= 4) ? 2 : 1;
+};
 
 template <typename FT, int C, int D1, int MODE>
-__global__ void __launch_bounds__(512) mttkrp_kernel(const MttkrpParams p) {
+__global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(const MttkrpParams p) {
     using E = Elem<FT>;
+    using Raw = typename E::Raw;
     constexpr int VEC = E::VEC;
-    constexpr int NARR = (MODE == M_PERM) ? 1 : (D1 + 2);
+    constexpr int DA = D1 > 0 ? D1 : 1;
+    constexpr int REC = record_words(D1 + 1);
+    constexpr int NARR = (MODE == M_PERM) ? 1 : (D1 + 2);          // SoA arrays staged
+    constexpr int WPE = (MODE == M_SORTED) ? REC : NARR;             // staged words / nonzero
     constexpr int LOADS = D1 * C;
-    constexpr int U = (LOADS <= 2) ? 4 : (LOADS <= 4 ? 2 : 1);
+    constexpr int U = (LOADS <= 2) ? 2 : 1;
     constexpr unsigned FULL = 0xffffffffu;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -82,7 +102,7 @@ __global__ void __launch_bounds__(512) mttkrp_kernel(const MttkrpParams p) {
     const int wpc = blockDim.x >> 5;
     const int npw = p.npw;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw) + 2 * warp;
-    int32_t *wbuf = reinterpret_cast<int32_t *>(smem_raw + 16 * wpc) + (size_t)warp * 2 * NARR * npw;
+    int32_t *wbuf = reinterpret_cast<int32_t *>(smem_raw + 16 * wpc) + (size_t)warp * 2 * WPE * npw;
 
     const int64_t gw = (int64_t)blockIdx.x * wpc + warp;
     const int64_t nw = (int64_t)gridDim.x * wpc;
@@ -106,16 +126,26 @@ __global__ void __launch_bounds__(512) mttkrp_kernel(const MttkrpParams p) {
     }
     __syncwarp();
 
+    auto chunk_len = [&](int64_t ch) {
+        const int64_t c0 = ch * npw;
+        return (int)(p.nnz - c0 < (int64_t)npw ? p.nnz - c0 : (int64_t)npw);
+    };
     // lane 0: stage the 16-byte-aligned body of chunk `ch` into stage `s`
     auto issue = [&](int64_t ch, int s) {
         const int64_t c0 = ch * npw;
-        const int n = (int)(p.nnz - c0 < (int64_t)npw ? p.nnz - c0 : (int64_t)npw);
-        const uint32_t bytes = (uint32_t)(n & ~3) * 4u;
-        int32_t *buf = wbuf + s * NARR * npw;
-        mbar_arrive_expect_tx(&bars[s], bytes * NARR);
-        if (bytes) {
+        const int n = chunk_len(ch);
+        int32_t *buf = wbuf + s * WPE * npw;
+        if (MODE == M_SORTED) {
+            const uint32_t bytes = (uint32_t)((n * REC) & ~3) * 4u;
+            mbar_arrive_expect_tx(&bars[s], bytes);
+            if (bytes) bulk_g2s(buf, p.rec + c0 * REC, bytes, &bars[s]);
+        } else {
+            const uint32_t bytes = (uint32_t)(n & ~3) * 4u;
+            mbar_arrive_expect_tx(&bars[s], bytes * NARR);
+            if (bytes) {
 #pragma unroll
-            for (int a = 0; a < NARR; ++a) bulk_g2s(buf + a * npw, src[a] + c0, bytes, &bars[s]);
+                for (int a = 0; a < NARR; ++a) bulk_g2s(buf + a * npw, src[a] + c0, bytes, &bars[s]);
+            }
         }
     };
     if (lane == 0) {
@@ -129,6 +159,7 @@ __global__ void __launch_bounds__(512) mttkrp_kernel(const MttkrpParams p) {
     const int g = lane >> log2L;
     const int l = lane & (L - 1);
     const int S = p.S;
+    const int rstride = p.fld * (int)sizeof(FT);  // bytes per factor row (< 2^31, checked on the host)
 
     int k = 0;
     for (int64_t ch = gw; ch < p.nchunks; ch += nw, ++k) {
@@ -142,13 +173,18 @@ __global__ void __launch_bounds__(512) mttkrp_kernel(const MttkrpParams p) {
             mbar_wait(&bars[s], parity);
             return;
         }
-        int32_t *buf = wbuf + s * NARR * npw;
+        int32_t *buf = wbuf + s * WPE * npw;
         const int64_t c0 = ch * npw;
-        const int n = (int)(p.nnz - c0 < (int64_t)npw ? p.nnz - c0 : (int64_t)npw);
-        const int nb = n & ~3;
-        if (lane < n - nb) {
+        const int n = chunk_len(ch);
+        if (MODE == M_SORTED) {  // words past the 16-byte body of a ragged chunk
+            const int W = n * REC, wb = W & ~3;
+            if (lane < W - wb) buf[wb + lane] = __ldg(p.rec + c0 * REC + wb + lane);
+        } else {
+            const int nb = n & ~3;
+            if (lane < n - nb) {
 #pragma unroll
-            for (int a = 0; a < NARR; ++a) buf[a * npw + nb + lane] = __ldg(src[a] + c0 + nb + lane);
+                for (int a = 0; a < NARR; ++a) buf[a * npw + nb + lane] = __ldg(src[a] + c0 + nb + lane);
+            }
         }
         __syncwarp();
 
@@ -157,7 +193,7 @@ __global__ void __launch_bounds__(512) mttkrp_kernel(const MttkrpParams p) {
         int crow0 = 0, crow1 = 0;
         if (MODE == M_SORTED) {
             crow0 = buf[0];
-            crow1 = buf[n - 1];
+            crow1 = buf[(n - 1) * REC];
         } else if (MODE == M_PERM) {
             crow0 = __ldg(p.rows + buf[0]);
             crow1 = __ldg(p.rows + buf[n - 1]);
@@ -166,6 +202,7 @@ __global__ void __launch_bounds__(512) mttkrp_kernel(const MttkrpParams p) {
         for (int rb = 0; rb < p.n_rb; ++rb) {
             int col[C], nv[C];
             float lam[C][VEC];
+            const char *fb[DA][C];  // this lane's column chunk of each factor
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 col[c] = rb * p.rb_cols + (c * L + l) * VEC;
@@ -173,6 +210,9 @@ __global__ void __launch_bounds__(512) mttkrp_kernel(const MttkrpParams p) {
 #pragma unroll
                 for (int v = 0; v < VEC; ++v)
                     lam[c][v] = (p.lambda && v < nv[c]) ? __ldg(p.lambda + col[c] + v) : 1.0f;
+#pragma unroll
+                for (int m = 0; m < D1; ++m)
+                    fb[m][c] = reinterpret_cast<const char *>(p.fac[m]) + (int64_t)col[c] * sizeof(FT);
             }
 
             float acc[C][VEC], facc[C][VEC];
@@ -189,9 +229,9 @@ __global__ void __launch_bounds__(512) mttkrp_kernel(const MttkrpParams p) {
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
                     if (nv[c] == 0) continue;
-                    float w[VEC];
+                    float w[VEC];  // columns >= R hold padding products: write zeros
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) w[v] = a[c][v] * lam[c][v];
+                    for (int v = 0; v < VEC; ++v) w[v] = v < nv[c] ? a[c][v] * lam[c][v] : 0.0f;
                     if (atomic) {
 #pragma unroll
                         for (int q = 0; q < VEC; q += 4) red_add4(dst + col[c] + q, w + q);
@@ -204,82 +244,123 @@ __global__ void __launch_bounds__(512) mttkrp_kernel(const MttkrpParams p) {
                 }
             };
 
-            for (int t0 = 0; t0 < cnt; t0 += U) {
-                int rowu[U];
-                float xu[U];
-                uint4 raw[U][D1 > 0 ? D1 : 1][C];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int t = t0 + u;
-                    const bool vu = t < cnt;
-                    const int e = e0 + (vu ? t : 0);
-                    int r[D1 > 0 ? D1 : 1];
-                    if (MODE == M_PERM) {
-                        const int q = buf[e];
-                        rowu[u] = __ldg(p.rows + q);
-                        xu[u] = __ldg(p.vals + q);
-#pragma unroll
-                        for (int m = 0; m < D1; ++m) r[m] = __ldg(p.oidx[m] + q);
+            // load one nonzero's row, value and its d-1 factor-row chunks
+            auto fetch = [&](int e, int &row, float &x, Raw (&rw)[DA][C]) {
+                int r[DA];
+                if (MODE == M_SORTED) {
+                    int w[REC];
+                    const int32_t *rp = buf + e * REC;
+                    if (REC == 4) {
+                        const int4 q = *reinterpret_cast<const int4 *>(rp);
+                        w[0] = q.x; w[1] = q.y; w[2] = q.z; w[3] = q.w;
                     } else {
-                        rowu[u] = buf[e];
-                        xu[u] = __int_as_float(buf[(D1 + 1) * npw + e]);
 #pragma unroll
-                        for (int m = 0; m < D1; ++m) r[m] = buf[(1 + m) * npw + e];
+                        for (int h = 0; h < REC; h += 2) {
+                            const int2 q = *reinterpret_cast<const int2 *>(rp + h);
+                            w[h] = q.x;
+                            w[h + 1] = q.y;
+                        }
                     }
+                    row = w[0];
 #pragma unroll
-                    for (int m = 0; m < D1; ++m) {
-                        const FT *base = reinterpret_cast<const FT *>(p.fac[m]) + (int64_t)r[m] * p.fld;
+                    for (int m = 0; m < D1; ++m) r[m] = w[1 + m];
+                    x = __int_as_float(w[D1 + 1]);
+                } else if (MODE == M_PERM) {
+                    const int q = buf[e];
+                    row = __ldg(p.rows + q);
+                    x = __ldg(p.vals + q);
 #pragma unroll
-                        for (int c = 0; c < C; ++c)
-                            raw[u][m][c] = (vu && nv[c] > 0) ? ldg16(base + col[c]) : make_uint4(0, 0, 0, 0);
-                    }
+                    for (int m = 0; m < D1; ++m) r[m] = __ldg(p.oidx[m] + q);
+                } else {
+                    row = buf[e];
+                    x = __int_as_float(buf[(D1 + 1) * npw + e]);
+#pragma unroll
+                    for (int m = 0; m < D1; ++m) r[m] = buf[(1 + m) * npw + e];
                 }
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (t0 + u >= cnt) break;
-                    float prod[C][VEC];
+                for (int m = 0; m < D1; ++m) {
 #pragma unroll
-                    for (int c = 0; c < C; ++c) {
+                    for (int c = 0; c < C; ++c)
+                        rw[m][c] = nv[c] > 0 ? E::load(fb[m][c] + (int64_t)r[m] * rstride) : Raw{};
+                }
+            };
+            // multiply out one nonzero and fold it into the running row sum;
+            // `vote`: every lane of the warp runs this step (uniform fast path)
+            auto step = [&](int row, float x, const Raw (&rw)[DA][C], bool vote) {
+                float part[C][VEC], fl[C][VEC];  // x * first D1-1 factors; last factor
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) prod[c][v] = xu[u];
+                for (int c = 0; c < C; ++c) {
 #pragma unroll
-                        for (int m = 0; m < D1; ++m) {
-                            float f[VEC];
-                            E::widen(raw[u][m][c], f);
+                    for (int v = 0; v < VEC; ++v) part[c][v] = x;
 #pragma unroll
-                            for (int v = 0; v < VEC; ++v) prod[c][v] *= f[v];
+                    for (int m = 0; m + 1 < D1; ++m) {
+                        float f[VEC];
+                        E::widen(rw[m][c], f);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) part[c][v] *= f[v];
+                    }
+                    if (D1 > 0) E::widen(rw[DA - 1][c], fl[c]);
+                }
+                const bool ch = row != cur;
+                const bool any = vote ? __any_sync(FULL, ch) : ch;
+                if (any && ch) {
+                    if (cur >= 0) {
+                        if (MODE == M_ATOMIC) {
+                            write_row(cur, acc, true);
+                        } else if (!fclosed) {
+                            fclosed = true;
+                            frow = cur;
+#pragma unroll
+                            for (int c = 0; c < C; ++c)
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) facc[c][v] = acc[c][v];
+                        } else {
+                            write_row(cur, acc, false);  // row lies inside this group's block
                         }
+                    }
+                    cur = row;
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
 #pragma unroll
                         for (int v = 0; v < VEC; ++v)
-                            if (v >= nv[c]) prod[c][v] = 0.0f;
-                    }
-                    const int row = rowu[u];
-                    if (row != cur) {
-                        if (cur >= 0) {
-                            if (MODE == M_ATOMIC) {
-                                write_row(cur, acc, true);
-                            } else if (!fclosed) {
-                                fclosed = true;
-                                frow = cur;
+                            acc[c][v] = D1 > 0 ? part[c][v] * fl[c][v] : part[c][v];
+                } else {
 #pragma unroll
-                                for (int c = 0; c < C; ++c)
+                    for (int c = 0; c < C; ++c)
 #pragma unroll
-                                    for (int v = 0; v < VEC; ++v) facc[c][v] = acc[c][v];
-                            } else {
-                                write_row(cur, acc, false);  // row lies inside this group's block
-                            }
-                        }
-                        cur = row;
+                        for (int v = 0; v < VEC; ++v)
+                            acc[c][v] = D1 > 0 ? fmaf(part[c][v], fl[c][v], acc[c][v])
+                                               : acc[c][v] + part[c][v];
+                }
+            };
+
+            if (n == npw) {
+                // full chunk: every group walks exactly S nonzeros, U at a time
+                int t = 0;
+                for (; t + U <= S; t += U) {
+                    int rowu[U];
+                    float xu[U];
+                    Raw raw[U][DA][C];
 #pragma unroll
-                        for (int c = 0; c < C; ++c)
+                    for (int u = 0; u < U; ++u) fetch(e0 + t + u, rowu[u], xu[u], raw[u]);
 #pragma unroll
-                            for (int v = 0; v < VEC; ++v) acc[c][v] = prod[c][v];
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < C; ++c)
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v) acc[c][v] += prod[c][v];
-                    }
+                    for (int u = 0; u < U; ++u) step(rowu[u], xu[u], raw[u], true);
+                }
+                for (; t < S; ++t) {
+                    int row;
+                    float x;
+                    Raw rw[DA][C];
+                    fetch(e0 + t, row, x, rw);
+                    step(row, x, rw, true);
+                }
+            } else {
+                // the tensor's last, ragged chunk: groups hold different counts
+                for (int t = 0; t < cnt; ++t) {
+                    int row;
+                    float x;
+                    Raw rw[DA][C];
+                    fetch(e0 + t, row, x, rw);
+                    step(row, x, rw, false);
                 }
             }
 

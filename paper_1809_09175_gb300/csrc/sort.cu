@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "mttkrp_kernel.cuh"
 
 namespace spt {
 
@@ -155,6 +156,23 @@ __global__ void gather_f32_kernel(const float *src, const int32_t *ord, int64_t 
 struct IdxPtrs {
     const int32_t *p[SPT_MAX_ORDER];
 };
+
+// Packed records of the mode-n sorted copy: rec[i] = {rows_sorted[i],
+// idx[m][perm[i]] for m != n in increasing m, bits(vals[perm[i]]), 0 pad}.
+__global__ void pack_records_kernel(IdxPtrs idx, int d, int n, const float *vals, const int32_t *perm,
+                                    const int32_t *srows, int64_t P, int rw, int32_t *rec) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = perm[i];
+        int32_t *r = rec + i * rw;
+        r[0] = srows[i];
+        int k = 1;
+        for (int m = 0; m < d; ++m)
+            if (m != n) r[k++] = idx.p[m][q];
+        r[k++] = __float_as_int(vals[q]);
+        for (; k < rw; ++k) r[k] = 0;
+    }
+}
 struct IdxOut {
     int32_t *p[SPT_MAX_ORDER];
 };
@@ -427,40 +445,27 @@ spt_status build_perm_mode(spt_tensor t, int n, bool index_only, cudaStream_t st
     const int d = t->d;
     // release an earlier build of this mode
     if (t->perm[n]) { cudaFreeAsync(t->perm[n], st); t->perm[n] = nullptr; }
-    if (t->sorted_buf[n]) {
-        cudaFreeAsync(t->sorted_buf[n], st);
-        t->sorted_buf[n] = nullptr;
-        for (int m = 0; m < SPT_MAX_ORDER; ++m) t->sidx[n][m] = nullptr;
-        t->svals[n] = nullptr;
-    }
-    int32_t *perm = nullptr;
+    if (t->sorted_buf[n]) { cudaFreeAsync(t->sorted_buf[n], st); t->sorted_buf[n] = nullptr; }
+    int32_t *perm = nullptr, *srows = nullptr;
     spt_status s = dmalloc((void **)&perm, seg_bytes(P, 4), st);
-    if (s) return s;
-    void *sbuf = nullptr;
-    int32_t *srows = nullptr;
-    const size_t seg = seg_bytes(P, 4);
-    if (!index_only) {
-        s = dmalloc(&sbuf, seg * (d + 1), st);
-        if (s) { dfree(perm, st); return s; }
-        srows = reinterpret_cast<int32_t *>((char *)sbuf + seg * n);
-    } else {
-        s = dmalloc((void **)&srows, seg, st);
-        if (s) { dfree(perm, st); return s; }
-    }
+    if (!s) s = dmalloc((void **)&srows, seg_bytes(P, 4), st);
+    if (s) { dfree(perm, st); return s; }
     const int bits = bit_width_u32((uint64_t)(t->dims[n] - 1));
     s = radix_sort_pairs(reinterpret_cast<const uint32_t *>(t->idx[n]), nullptr, P, bits,
                          reinterpret_cast<uint32_t *>(srows), perm, st);
-    if (s) { dfree(perm, st); dfree(index_only ? (void *)srows : sbuf, st); return s; }
+    if (s) { dfree(perm, st); dfree(srows, st); return s; }
     const int g = grid_for(P, 256);
     if (!index_only) {
-        for (int m = 0; m < d; ++m) {
-            int32_t *dst = reinterpret_cast<int32_t *>((char *)sbuf + seg * m);
-            t->sidx[n][m] = dst;
-            if (m != n && P > 0) gather_i32_kernel<<<g, 256, 0, st>>>(t->idx[m], perm, P, dst);
-        }
-        t->svals[n] = reinterpret_cast<float *>((char *)sbuf + seg * d);
-        if (P > 0) gather_f32_kernel<<<g, 256, 0, st>>>(t->vals, perm, P, t->svals[n]);
-        SPT_LAUNCH_CHECK("gather kernels");
+        const int rw = record_words(d);
+        void *sbuf = nullptr;
+        s = dmalloc(&sbuf, seg_bytes(P * rw, 4), st);
+        if (s) { dfree(perm, st); dfree(srows, st); return s; }
+        IdxPtrs ip;
+        for (int m = 0; m < d; ++m) ip.p[m] = t->idx[m];
+        if (P > 0)
+            pack_records_kernel<<<g, 256, 0, st>>>(ip, d, n, t->vals, perm, srows, P, rw,
+                                                   reinterpret_cast<int32_t *>(sbuf));
+        SPT_LAUNCH_CHECK("pack_records_kernel");
         t->sorted_buf[n] = sbuf;
     }
     t->perm[n] = perm;
@@ -469,7 +474,7 @@ spt_status build_perm_mode(spt_tensor t, int n, bool index_only, cudaStream_t st
     StatAcc *acc = nullptr;
     s = dmalloc((void **)&cnt, 4 * t->dims[n], st);
     if (!s) s = dmalloc((void **)&acc, sizeof(StatAcc), st);
-    if (s) { if (index_only) dfree(srows, st); dfree(cnt, st); return s; }
+    if (s) { dfree(srows, st); dfree(cnt, st); return s; }
     SPT_CUDA(cudaMemsetAsync(cnt, 0, 4 * t->dims[n], st));
     SPT_CUDA(cudaMemsetAsync(acc, 0, sizeof(StatAcc), st));
     if (P > 0) {
@@ -482,7 +487,7 @@ spt_status build_perm_mode(spt_tensor t, int n, bool index_only, cudaStream_t st
     SPT_CUDA(cudaMemcpyAsync(&h, acc, sizeof(StatAcc), cudaMemcpyDeviceToHost, st));
     dfree(cnt, st);
     dfree(acc, st);
-    if (index_only) dfree(srows, st);
+    dfree(srows, st);
     SPT_CUDA(cudaStreamSynchronize(st));
     ModeStats &ms = t->stats[n];
     ms.valid = true;

@@ -152,7 +152,9 @@ def test_graph_replay_matches_direct_launch_and_resume():
     dims = (500, 400, 300, 20)
     idx, vals = synth.coo_zipf(dims, 80_000, 1.1, 5)
     R = 24
-    facs_np = synth.factor_matrices(dims, R, 5, "uniform")
+    # N(0,1) starting factors keep the Gram-Hadamard systems well conditioned,
+    # so the comparison measures replay equivalence, not conditioning
+    facs_np = synth.factor_matrices(dims, R, 5, "normal")
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         T, facs, lam, fit, ws = _setup(P, idx, vals, dims, R, facs_np)

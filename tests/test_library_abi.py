@@ -64,7 +64,7 @@ def test_paper_sizes_table_matches_golden():
     # the schedule built from the table covers FBS columns with 16-byte chunks
     for R in (1, 16, 24, 48, 64, 96, 128, 200):
         vs, fbs = P.mttkrp_paper_sizes(R)
-        for fdt, vec in (("f32", 4), ("bf16", 8)):
+        for fdt, vec in (("f32", 4), ("bf16", 4)):
             s = P.mttkrp_paper_schedule(R, fdt, "sorted")
             cover = s.lanes_per_nnz * s.chunks * vec
             assert cover >= fbs and s.nnz_per_group == 128 and s.warps_per_cta == 4
