@@ -202,6 +202,134 @@ spt_status mttkrp_paper_sizes(int rank, int *vector_size, int *fbs);
  * mapped onto this kernel's schedule for the given scatter strategy. */
 spt_status mttkrp_paper_schedule(int rank, spt_dtype fdt, int scatter, spt_schedule *out);
 
+/* ---- schedule search: candidates, autotuner, features, learned selector -- */
+/* Not in the paper, whose schedule is the fixed rule of Tab. "sizes". */
+
+#define SPT_NUM_CANDIDATES 36 /* fixed list of candidate schedules per (tensor, mode, rank) */
+#define SPT_NUM_FEATURES 12   /* per-mode features of tensor_mode_features() */
+
+/* The candidate schedules for rank R (host logic): candidate q combines a
+ * scatter strategy (sorted / atomic / perm), a lane layout (ceil(R/4) lanes
+ * rounded to a power of two with one chunk, or half as many lanes with two
+ * chunks), about 96, 192 or 384 nonzeros per warp chunk, and 4 or 8 warps per
+ * CTA.  out: SPT_NUM_CANDIDATES schedules; valid (nullable): 1 where the
+ * candidate can run on this tensor (its permutation / copy is built, it fits
+ * shared memory). */
+spt_status mttkrp_candidates(spt_tensor t, int mode, int rank, spt_schedule *out, int *valid);
+
+/* Time one schedule: a warm-up launch, then the fastest of `reps` launches
+ * (CUDA events).  Arguments as mttkrp(); synchronises `stream`. *ms in ms. */
+spt_status mttkrp_time_schedule(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt,
+                                int rank, int ld, float *out, const spt_schedule *sched, int reps,
+                                float *ms, void *stream);
+
+/* Exhaustive autotuner: time every valid candidate (mttkrp_time_schedule)
+ * and return the fastest in *best (and its time in *best_ms).  times
+ * (nullable, SPT_NUM_CANDIDATES floats, host) receives every candidate's
+ * time, -1 for invalid ones: the training data of the learned selector.
+ * `out` is scratch output (I_mode x ld float32).  Synchronises `stream`. */
+spt_status mttkrp_autotune(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt, int rank,
+                           int ld, float *out, int reps, spt_schedule *best, float *best_ms,
+                           float *times, void *stream);
+
+/* Per-mode features (host output, SPT_NUM_FEATURES floats): order, log2 I_n,
+ * log2 prod_{m != n} I_m, log2 P, log2 R, factor element bytes, log2 of the
+ * hottest slice over the mean nonempty slice, coefficient of variation of the
+ * slice sizes, hottest-slice share of P, nonempty-slice fraction, log2 of the
+ * mean run length of equal mode-n coordinates in storage order, and log2 of
+ * the other factors' bytes over the 129 MB L2.  Needs build_mode_permutation(mode). */
+spt_status tensor_mode_features(spt_tensor t, int mode, int rank, spt_dtype fdt, float *feat);
+
+/* Sizes of the selector network h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2),
+ * y = W3 h2 + b3 with parameters packed W1 (H1 x F), b1, W2 (H2 x H1), b2,
+ * W3 (K x H2), b3 (row-major, float32). */
+int64_t mlp_param_count(int F, int H1, int H2, int K);
+/* Floats of the `work` buffer mlp_forward / mlp_loss_grad need for B samples. */
+int64_t mlp_workspace_floats(int B, int F, int H1, int H2, int K);
+
+/* Forward pass for B samples (rows of X, B x F, device) into Y (B x K). */
+spt_status mlp_forward(int B, int F, int H1, int H2, int K, const float *X, const float *params,
+                       float *Y, float *work, void *stream);
+
+/* Masked mean-squared error L = sum M (Y - T)^2 / sum M and its gradient
+ * with respect to every parameter (packed like params) by back-propagation;
+ * *loss is a device float.  All pointers device. */
+spt_status mlp_loss_grad(int B, int F, int H1, int H2, int K, const float *X, const float *params,
+                         const float *T, const float *M, float *grads, float *loss, float *work,
+                         void *stream);
+
+/* One Adam step (bias-corrected, step >= 1) on n parameters. */
+spt_status mlp_adam(int64_t n, float *params, const float *grads, float *m, float *v, float lr,
+                    float beta1, float beta2, float eps, int step, void *stream);
+
+/* Fused one-CTA inference for a few samples (the selector's path). */
+spt_status mlp_infer(int B, int F, int H1, int H2, int K, const float *X, const float *params,
+                     float *Y, void *stream);
+
+/* A trained selector: F = SPT_NUM_FEATURES, K = SPT_NUM_CANDIDATES, params
+ * on the device; mean / std (host, F floats, nullable) normalise features. */
+typedef struct {
+    int F, H1, H2, K;
+    const float *params;
+    const float *mean;
+    const float *std;
+} spt_selector;
+
+/* Choose a schedule with a trained selector: features -> network (own
+ * inference kernel) -> the valid candidate with the smallest predicted time.
+ * pred (nullable, host, SPT_NUM_CANDIDATES) receives the predictions.
+ * Synchronises `stream`. */
+spt_status mttkrp_select(spt_tensor t, int mode, spt_dtype fdt, int rank, const spt_selector *sel,
+                         spt_schedule *out, float *pred, void *stream);
+
+/* ---- batched MTTKRP: many tensors, all modes, one persistent launch ----- */
+
+typedef struct spt_batch_s *spt_batch; /* opaque, library-owned */
+
+/* One tensor of a batch.  The MTTKRP definition is that of mttkrp() (unit
+ * weights); the traversal is the permuted one over the mode-sorted copy
+ * (Sec. 5), so every listed mode needs build_mode_permutation() without
+ * SPT_PERM_INDEX_ONLY.
+ *  tensor  : order 2..5.   mode : -1 = every mode, else one mode.
+ *  rank, ld: as for mttkrp(); factors and outputs share ld.
+ *  factors : host array of d device pointers (the batch's dtype), I_m x ld.
+ *  outs    : host array of device float32 outputs I_n x ld: d entries for
+ *            mode -1 (outs[n] for mode n), else one entry.
+ *  scheds  : NULL for the library choice, else d entries (or one for a
+ *            single mode); their scatter field is ignored. */
+typedef struct {
+    spt_tensor tensor;
+    int mode;
+    int rank;
+    int ld;
+    const void *const *factors;
+    float *const *outs;
+    const spt_schedule *scheds;
+} spt_batch_item;
+
+/* Build a batch: one task per (tensor, mode), whose chunks of nonzeros form
+ * one work list.  Copies the task table to the device (synchronous); the
+ * pointers are captured, so the tensors, factors and outputs must outlive
+ * the batch and keep their addresses. */
+spt_status mttkrp_batch_create(int count, const spt_batch_item *items, spt_dtype fdt, spt_batch *out);
+
+/* Run every task: one zero-fill kernel for the outputs, then one persistent
+ * kernel whose warps claim chunks from a device counter.  On a non-default
+ * stream the two launches are captured in a CUDA graph at the first call and
+ * replayed afterwards; on the legacy default stream they are launched
+ * directly. */
+spt_status mttkrp_batch_run(spt_batch b, void *stream);
+
+/* Tasks, work items (chunks) and persistent CTAs of a batch. Host outputs. */
+spt_status mttkrp_batch_info(spt_batch b, int64_t *tasks, int64_t *items, int *blocks);
+
+/* Synchronise `stream` and read the batch kernel's status word (SPT_ETIMEOUT
+ * if a bounded wait ran out). */
+spt_status mttkrp_batch_check(spt_batch b, void *stream);
+
+/* Free a batch (synchronises the device). */
+spt_status mttkrp_batch_destroy(spt_batch b);
+
 /* ---- CP-ALS (Sec. 2) -------------------------------------------------- */
 
 /* Workspace bytes cp_als_step needs for this tensor, rank and ld. */

@@ -51,6 +51,18 @@ class spt_schedule(C.Structure):
         return cls(scatter, lanes_per_nnz, chunks, nnz_per_group, warps_per_cta, ctas_per_sm)
 
 
+class spt_selector(C.Structure):
+    _fields_ = [("F", C.c_int), ("H1", C.c_int), ("H2", C.c_int), ("K", C.c_int),
+                ("params", C.c_void_p), ("mean", C.POINTER(C.c_float)),
+                ("std", C.POINTER(C.c_float))]
+
+
+class spt_batch_item(C.Structure):
+    _fields_ = [("tensor", C.c_void_p), ("mode", C.c_int), ("rank", C.c_int), ("ld", C.c_int),
+                ("factors", C.POINTER(C.c_void_p)), ("outs", C.POINTER(C.c_void_p)),
+                ("scheds", C.POINTER(spt_schedule))]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: run paper_1809_09175_gb300/build.py (or "
                       "__graft_entry__.build()) to compile the CUDA library")
@@ -106,6 +118,32 @@ _try_sig("cp_als_step", _vp, C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _vp, _vp
          C.c_size_t, _vp)
 _try_sig("cp_als_status", _vp, _vp)
 _try_sig("mode_permutation_noalloc", _vp, C.c_int64, C.c_int64, _vp, _vp)
+SPT_NUM_CANDIDATES, SPT_NUM_FEATURES = 36, 12
+_fp = C.POINTER(C.c_float)
+_try_sig("mttkrp_candidates", _vp, C.c_int, C.c_int, C.POINTER(spt_schedule), C.POINTER(C.c_int))
+_try_sig("mttkrp_time_schedule", _vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _vp,
+         C.POINTER(spt_schedule), C.c_int, _fp, _vp)
+_try_sig("mttkrp_autotune", _vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _vp, C.c_int,
+         C.POINTER(spt_schedule), _fp, _fp, _vp)
+_try_sig("tensor_mode_features", _vp, C.c_int, C.c_int, C.c_int, _fp)
+_try_sig("mlp_forward", C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp)
+_try_sig("mlp_loss_grad", C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp,
+         _vp, _vp, _vp)
+_try_sig("mlp_adam", C.c_int64, _vp, _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, C.c_float,
+         C.c_int, _vp)
+_try_sig("mlp_infer", C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp)
+_try_sig("mttkrp_select", _vp, C.c_int, C.c_int, C.c_int, C.POINTER(spt_selector),
+         C.POINTER(spt_schedule), _fp, _vp)
+for _n in ("mlp_param_count", "mlp_workspace_floats"):
+    getattr(_L, _n).restype = C.c_int64
+_L.mlp_param_count.argtypes = [C.c_int] * 4
+_L.mlp_workspace_floats.argtypes = [C.c_int] * 5
+EXPORTED += ["mlp_param_count", "mlp_workspace_floats"]
+_try_sig("mttkrp_batch_create", C.c_int, C.POINTER(spt_batch_item), C.c_int, C.POINTER(_vp))
+_try_sig("mttkrp_batch_run", _vp, _vp)
+_try_sig("mttkrp_batch_info", _vp, _i64p, _i64p, C.POINTER(C.c_int))
+_try_sig("mttkrp_batch_check", _vp, _vp)
+_try_sig("mttkrp_batch_destroy", _vp)
 SPT_NOALLOC_MAX_NNZ = 1835008
 
 
@@ -234,3 +272,108 @@ def mode_permutation_noalloc(keys_ptr: int, n: int, dim: int, perm_ptr: int, str
     """Mode permutation computed in the library's static scratch area, for
     callers that cannot allocate device memory (see include/spt.h)."""
     _chk(_L.mode_permutation_noalloc(keys_ptr or None, n, dim, perm_ptr or None, stream or None))
+
+
+def mttkrp_batch_create(items, fdt):
+    """items: list of dicts with tensor (handle), mode, rank, ld, factors
+    (list of device pointers), outs (list of device pointers), scheds (list of
+    spt_schedule or None).  Returns (batch handle, keep-alive list)."""
+    arr = (spt_batch_item * len(items))()
+    keep = []
+    for q, it in enumerate(items):
+        f = _ptrs(it["factors"])
+        o = _ptrs(it["outs"])
+        keep += [f, o]
+        sc = None
+        if it.get("scheds") is not None:
+            sc = (spt_schedule * len(it["scheds"]))(*it["scheds"])
+            keep.append(sc)
+        arr[q] = spt_batch_item(it["tensor"], it.get("mode", -1), it["rank"], it["ld"], f, o,
+                                C.cast(sc, C.POINTER(spt_schedule)) if sc is not None else None)
+    keep.append(arr)
+    out = _vp()
+    _chk(_L.mttkrp_batch_create(len(items), arr, _dt(fdt), C.byref(out)))
+    return out.value, keep
+
+
+def mttkrp_batch_run(b: int, stream: int = 0):
+    _chk(_L.mttkrp_batch_run(b, stream or None))
+
+
+def mttkrp_batch_info(b: int):
+    t, i, k = C.c_int64(), C.c_int64(), C.c_int()
+    _chk(_L.mttkrp_batch_info(b, C.byref(t), C.byref(i), C.byref(k)))
+    return t.value, i.value, k.value
+
+
+def mttkrp_batch_check(b: int, stream: int = 0):
+    _chk(_L.mttkrp_batch_check(b, stream or None))
+
+
+def mttkrp_batch_destroy(b: int):
+    _chk(_L.mttkrp_batch_destroy(b))
+
+
+def mttkrp_candidates(t: int, mode: int, rank: int):
+    """Returns (list of spt_schedule, list of 0/1 valid flags)."""
+    out = (spt_schedule * SPT_NUM_CANDIDATES)()
+    valid = (C.c_int * SPT_NUM_CANDIDATES)()
+    _chk(_L.mttkrp_candidates(t, mode, rank, out, valid))
+    return list(out), list(valid)
+
+
+def mttkrp_time_schedule(t, mode, factor_ptrs, fdt, rank, ld, out_ptr, sched, reps=3, stream=0):
+    ms = C.c_float()
+    _chk(_L.mttkrp_time_schedule(t, mode, _ptrs(factor_ptrs), _dt(fdt), rank, ld, out_ptr,
+                                 C.byref(sched), reps, C.byref(ms), stream or None))
+    return ms.value
+
+
+def mttkrp_autotune(t, mode, factor_ptrs, fdt, rank, ld, out_ptr, reps=2, stream=0):
+    """Returns (best spt_schedule, best ms, list of per-candidate ms; -1 invalid)."""
+    best = spt_schedule()
+    bms = C.c_float()
+    times = (C.c_float * SPT_NUM_CANDIDATES)()
+    _chk(_L.mttkrp_autotune(t, mode, _ptrs(factor_ptrs), _dt(fdt), rank, ld, out_ptr, reps,
+                            C.byref(best), C.byref(bms), times, stream or None))
+    return best, bms.value, list(times)
+
+
+def tensor_mode_features(t, mode, rank, fdt):
+    f = (C.c_float * SPT_NUM_FEATURES)()
+    _chk(_L.tensor_mode_features(t, mode, rank, _dt(fdt), f))
+    return list(f)
+
+
+def mlp_param_count(F, H1, H2, K):
+    return int(_L.mlp_param_count(F, H1, H2, K))
+
+
+def mlp_workspace_floats(B, F, H1, H2, K):
+    return int(_L.mlp_workspace_floats(B, F, H1, H2, K))
+
+
+def mlp_forward(B, F, H1, H2, K, X_ptr, params_ptr, Y_ptr, work_ptr, stream=0):
+    _chk(_L.mlp_forward(B, F, H1, H2, K, X_ptr, params_ptr, Y_ptr, work_ptr, stream or None))
+
+
+def mlp_loss_grad(B, F, H1, H2, K, X_ptr, params_ptr, T_ptr, M_ptr, grads_ptr, loss_ptr, work_ptr,
+                  stream=0):
+    _chk(_L.mlp_loss_grad(B, F, H1, H2, K, X_ptr, params_ptr, T_ptr, M_ptr, grads_ptr, loss_ptr,
+                          work_ptr, stream or None))
+
+
+def mlp_adam(n, params_ptr, grads_ptr, m_ptr, v_ptr, lr, beta1, beta2, eps, step, stream=0):
+    _chk(_L.mlp_adam(n, params_ptr, grads_ptr, m_ptr, v_ptr, lr, beta1, beta2, eps, step,
+                     stream or None))
+
+
+def mlp_infer(B, F, H1, H2, K, X_ptr, params_ptr, Y_ptr, stream=0):
+    _chk(_L.mlp_infer(B, F, H1, H2, K, X_ptr, params_ptr, Y_ptr, stream or None))
+
+
+def mttkrp_select(t, mode, fdt, rank, sel: "spt_selector", stream=0):
+    out = spt_schedule()
+    pred = (C.c_float * SPT_NUM_CANDIDATES)()
+    _chk(_L.mttkrp_select(t, mode, _dt(fdt), rank, C.byref(sel), C.byref(out), pred, stream or None))
+    return out, list(pred)

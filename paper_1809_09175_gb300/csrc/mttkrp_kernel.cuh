@@ -83,17 +83,274 @@ template <typename FT, int C> struct MinBlocks {
     static constexpr int value = (Elem<FT>::VEC * C <= 4) ? 2 : 1;
 };
 
+// Compute one staged chunk of n nonzeros (n <= npw) for every rank block:
+// gather, multiply, segmented accumulate and write (see the file comment).
 template <typename FT, int C, int D1, int MODE>
-__global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(const MttkrpParams p) {
+__device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_t *buf, int n) {
     using E = Elem<FT>;
     using Raw = typename E::Raw;
     constexpr int VEC = E::VEC;
     constexpr int DA = D1 > 0 ? D1 : 1;
     constexpr int REC = record_words(D1 + 1);
-    constexpr int NARR = (MODE == M_PERM) ? 1 : (D1 + 2);          // SoA arrays staged
-    constexpr int WPE = (MODE == M_SORTED) ? REC : NARR;             // staged words / nonzero
     constexpr int LOADS = D1 * C;
     constexpr int U = (LOADS <= 2) ? 2 : 1;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int npw = p.npw;
+    const int log2L = p.log2L;
+    const int L = 1 << log2L;
+    const int G = 32 >> log2L;
+    const int g = lane >> log2L;
+    const int l = lane & (L - 1);
+    const int S = p.S;
+    const int rstride = p.fld * (int)sizeof(FT);  // bytes per factor row (< 2^31, checked on the host)
+
+    const int e0 = g * S;
+    const int cnt = max(0, min(S, n - e0));
+    int crow0 = 0, crow1 = 0;
+    if (MODE == M_SORTED) {
+        crow0 = buf[0];
+        crow1 = buf[(n - 1) * REC];
+    } else if (MODE == M_PERM) {
+        crow0 = __ldg(p.rows + buf[0]);
+        crow1 = __ldg(p.rows + buf[n - 1]);
+    }
+
+    for (int rb = 0; rb < p.n_rb; ++rb) {
+        int col[C], nv[C];
+        float lam[C][VEC];
+        const char *fb[DA][C];  // this lane's column chunk of each factor
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            col[c] = rb * p.rb_cols + (c * L + l) * VEC;
+            nv[c] = max(0, min(VEC, p.R - col[c]));
+#pragma unroll
+            for (int v = 0; v < VEC; ++v)
+                lam[c][v] = (p.lambda && v < nv[c]) ? __ldg(p.lambda + col[c] + v) : 1.0f;
+#pragma unroll
+            for (int m = 0; m < D1; ++m)
+                fb[m][c] = reinterpret_cast<const char *>(p.fac[m]) + (int64_t)col[c] * sizeof(FT);
+        }
+
+        float acc[C][VEC], facc[C][VEC];
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[c][v] = facc[c][v] = 0.0f;
+        int cur = -1, frow = -1;
+        bool fclosed = false;
+
+        // emit a finished row sum: atomic for shared rows, plain store otherwise
+        auto write_row = [&](int row, float (&a)[C][VEC], bool atomic) {
+            float *dst = p.out + (int64_t)row * p.old;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                if (nv[c] == 0) continue;
+                float w[VEC];  // columns >= R hold padding products: write zeros
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) w[v] = v < nv[c] ? a[c][v] * lam[c][v] : 0.0f;
+                if (atomic) {
+#pragma unroll
+                    for (int q = 0; q < VEC; q += 4) red_add4(dst + col[c] + q, w + q);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < VEC; q += 4)
+                        *reinterpret_cast<float4 *>(dst + col[c] + q) =
+                            make_float4(w[q], w[q + 1], w[q + 2], w[q + 3]);
+                }
+            }
+        };
+
+        // load one nonzero's row, value and its d-1 factor-row chunks
+        auto fetch = [&](int e, int &row, float &x, Raw (&rw)[DA][C]) {
+            int r[DA];
+            if (MODE == M_SORTED) {
+                int w[REC];
+                const int32_t *rp = buf + e * REC;
+                if (REC == 4) {
+                    const int4 q = *reinterpret_cast<const int4 *>(rp);
+                    w[0] = q.x; w[1] = q.y; w[2] = q.z; w[3] = q.w;
+                } else {
+#pragma unroll
+                    for (int h = 0; h < REC; h += 2) {
+                        const int2 q = *reinterpret_cast<const int2 *>(rp + h);
+                        w[h] = q.x;
+                        w[h + 1] = q.y;
+                    }
+                }
+                row = w[0];
+#pragma unroll
+                for (int m = 0; m < D1; ++m) r[m] = w[1 + m];
+                x = __int_as_float(w[D1 + 1]);
+            } else if (MODE == M_PERM) {
+                const int q = buf[e];
+                row = __ldg(p.rows + q);
+                x = __ldg(p.vals + q);
+#pragma unroll
+                for (int m = 0; m < D1; ++m) r[m] = __ldg(p.oidx[m] + q);
+            } else {
+                row = buf[e];
+                x = __int_as_float(buf[(D1 + 1) * npw + e]);
+#pragma unroll
+                for (int m = 0; m < D1; ++m) r[m] = buf[(1 + m) * npw + e];
+            }
+#pragma unroll
+            for (int m = 0; m < D1; ++m) {
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    rw[m][c] = nv[c] > 0 ? E::load(fb[m][c] + (int64_t)r[m] * rstride) : Raw{};
+            }
+        };
+        // multiply out one nonzero and fold it into the running row sum;
+        // `vote`: every lane of the warp runs this step (uniform fast path)
+        auto step = [&](int row, float x, const Raw (&rw)[DA][C], bool vote) {
+            float part[C][VEC], fl[C][VEC];  // x * first D1-1 factors; last factor
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) part[c][v] = x;
+#pragma unroll
+                for (int m = 0; m + 1 < D1; ++m) {
+                    float f[VEC];
+                    E::widen(rw[m][c], f);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) part[c][v] *= f[v];
+                }
+                if (D1 > 0) E::widen(rw[DA - 1][c], fl[c]);
+            }
+            const bool ch = row != cur;
+            const bool any = vote ? __any_sync(FULL, ch) : ch;
+            if (any && ch) {
+                if (cur >= 0) {
+                    if (MODE == M_ATOMIC) {
+                        write_row(cur, acc, true);
+                    } else if (!fclosed) {
+                        fclosed = true;
+                        frow = cur;
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) facc[c][v] = acc[c][v];
+                    } else {
+                        write_row(cur, acc, false);  // row lies inside this group's block
+                    }
+                }
+                cur = row;
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v)
+                        acc[c][v] = D1 > 0 ? part[c][v] * fl[c][v] : part[c][v];
+            } else {
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v)
+                        acc[c][v] = D1 > 0 ? fmaf(part[c][v], fl[c][v], acc[c][v])
+                                           : acc[c][v] + part[c][v];
+            }
+        };
+
+        if (n == npw) {
+            // full chunk: every group walks exactly S nonzeros, U at a time
+            int t = 0;
+            for (; t + U <= S; t += U) {
+                int rowu[U];
+                float xu[U];
+                Raw raw[U][DA][C];
+#pragma unroll
+                for (int u = 0; u < U; ++u) fetch(e0 + t + u, rowu[u], xu[u], raw[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) step(rowu[u], xu[u], raw[u], true);
+            }
+            for (; t < S; ++t) {
+                int row;
+                float x;
+                Raw rw[DA][C];
+                fetch(e0 + t, row, x, rw);
+                step(row, x, rw, true);
+            }
+        } else {
+            // the tensor's last, ragged chunk: groups hold different counts
+            for (int t = 0; t < cnt; ++t) {
+                int row;
+                float x;
+                Raw rw[DA][C];
+                fetch(e0 + t, row, x, rw);
+                step(row, x, rw, false);
+            }
+        }
+
+        if (MODE == M_ATOMIC) {
+            if (cur >= 0) write_row(cur, acc, true);
+        } else {
+            // Segmented combine of the groups' open runs, in group order.
+            // Every lane tracks the running (orow, oacc) for its columns;
+            // group 0's lanes perform the writes.
+            float oacc[C][VEC];
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) oacc[c][v] = 0.0f;
+            int orow = -1;
+            const bool writer = (g == 0);
+            auto emit = [&](int row, float (&a)[C][VEC]) {
+                if (writer) write_row(row, a, row == crow0 || row == crow1);
+            };
+            for (int g2 = 0; g2 < G; ++g2) {
+                const int srcl = (g2 << log2L) | l;
+                const int scur = __shfl_sync(FULL, cur, srcl);
+                if (scur < 0) break;  // this and later groups got no nonzeros
+                const int sfc = __shfl_sync(FULL, (int)fclosed, srcl);
+                const int sfrow = __shfl_sync(FULL, frow, srcl);
+                float F[C][VEC], A[C][VEC];
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        F[c][v] = __shfl_sync(FULL, facc[c][v], srcl);
+                        A[c][v] = __shfl_sync(FULL, acc[c][v], srcl);
+                    }
+                if (sfc) {
+                    if (orow == sfrow) {
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) F[c][v] += oacc[c][v];
+                    } else if (orow >= 0) {
+                        emit(orow, oacc);
+                    }
+                    emit(sfrow, F);
+                    orow = scur;
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) oacc[c][v] = A[c][v];
+                } else if (orow == scur) {
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) oacc[c][v] += A[c][v];
+                } else {
+                    if (orow >= 0) emit(orow, oacc);
+                    orow = scur;
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) oacc[c][v] = A[c][v];
+                }
+            }
+            if (orow >= 0) emit(orow, oacc);
+        }
+    }
+
+}
+
+template <typename FT, int C, int D1, int MODE>
+__global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(const MttkrpParams p) {
+    constexpr int REC = record_words(D1 + 1);
+    constexpr int NARR = (MODE == M_PERM) ? 1 : (D1 + 2);          // SoA arrays staged
+    constexpr int WPE = (MODE == M_SORTED) ? REC : NARR;             // staged words / nonzero
     constexpr unsigned FULL = 0xffffffffu;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -153,14 +410,6 @@ __global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(co
         if (gw + nw < p.nchunks) issue(gw + nw, 1);
     }
 
-    const int log2L = p.log2L;
-    const int L = 1 << log2L;
-    const int G = 32 >> log2L;
-    const int g = lane >> log2L;
-    const int l = lane & (L - 1);
-    const int S = p.S;
-    const int rstride = p.fld * (int)sizeof(FT);  // bytes per factor row (< 2^31, checked on the host)
-
     int k = 0;
     for (int64_t ch = gw; ch < p.nchunks; ch += nw, ++k) {
         const int s = k & 1;
@@ -188,244 +437,7 @@ __global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(co
         }
         __syncwarp();
 
-        const int e0 = g * S;
-        const int cnt = max(0, min(S, n - e0));
-        int crow0 = 0, crow1 = 0;
-        if (MODE == M_SORTED) {
-            crow0 = buf[0];
-            crow1 = buf[(n - 1) * REC];
-        } else if (MODE == M_PERM) {
-            crow0 = __ldg(p.rows + buf[0]);
-            crow1 = __ldg(p.rows + buf[n - 1]);
-        }
-
-        for (int rb = 0; rb < p.n_rb; ++rb) {
-            int col[C], nv[C];
-            float lam[C][VEC];
-            const char *fb[DA][C];  // this lane's column chunk of each factor
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                col[c] = rb * p.rb_cols + (c * L + l) * VEC;
-                nv[c] = max(0, min(VEC, p.R - col[c]));
-#pragma unroll
-                for (int v = 0; v < VEC; ++v)
-                    lam[c][v] = (p.lambda && v < nv[c]) ? __ldg(p.lambda + col[c] + v) : 1.0f;
-#pragma unroll
-                for (int m = 0; m < D1; ++m)
-                    fb[m][c] = reinterpret_cast<const char *>(p.fac[m]) + (int64_t)col[c] * sizeof(FT);
-            }
-
-            float acc[C][VEC], facc[C][VEC];
-#pragma unroll
-            for (int c = 0; c < C; ++c)
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) acc[c][v] = facc[c][v] = 0.0f;
-            int cur = -1, frow = -1;
-            bool fclosed = false;
-
-            // emit a finished row sum: atomic for shared rows, plain store otherwise
-            auto write_row = [&](int row, float (&a)[C][VEC], bool atomic) {
-                float *dst = p.out + (int64_t)row * p.old;
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    if (nv[c] == 0) continue;
-                    float w[VEC];  // columns >= R hold padding products: write zeros
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) w[v] = v < nv[c] ? a[c][v] * lam[c][v] : 0.0f;
-                    if (atomic) {
-#pragma unroll
-                        for (int q = 0; q < VEC; q += 4) red_add4(dst + col[c] + q, w + q);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < VEC; q += 4)
-                            *reinterpret_cast<float4 *>(dst + col[c] + q) =
-                                make_float4(w[q], w[q + 1], w[q + 2], w[q + 3]);
-                    }
-                }
-            };
-
-            // load one nonzero's row, value and its d-1 factor-row chunks
-            auto fetch = [&](int e, int &row, float &x, Raw (&rw)[DA][C]) {
-                int r[DA];
-                if (MODE == M_SORTED) {
-                    int w[REC];
-                    const int32_t *rp = buf + e * REC;
-                    if (REC == 4) {
-                        const int4 q = *reinterpret_cast<const int4 *>(rp);
-                        w[0] = q.x; w[1] = q.y; w[2] = q.z; w[3] = q.w;
-                    } else {
-#pragma unroll
-                        for (int h = 0; h < REC; h += 2) {
-                            const int2 q = *reinterpret_cast<const int2 *>(rp + h);
-                            w[h] = q.x;
-                            w[h + 1] = q.y;
-                        }
-                    }
-                    row = w[0];
-#pragma unroll
-                    for (int m = 0; m < D1; ++m) r[m] = w[1 + m];
-                    x = __int_as_float(w[D1 + 1]);
-                } else if (MODE == M_PERM) {
-                    const int q = buf[e];
-                    row = __ldg(p.rows + q);
-                    x = __ldg(p.vals + q);
-#pragma unroll
-                    for (int m = 0; m < D1; ++m) r[m] = __ldg(p.oidx[m] + q);
-                } else {
-                    row = buf[e];
-                    x = __int_as_float(buf[(D1 + 1) * npw + e]);
-#pragma unroll
-                    for (int m = 0; m < D1; ++m) r[m] = buf[(1 + m) * npw + e];
-                }
-#pragma unroll
-                for (int m = 0; m < D1; ++m) {
-#pragma unroll
-                    for (int c = 0; c < C; ++c)
-                        rw[m][c] = nv[c] > 0 ? E::load(fb[m][c] + (int64_t)r[m] * rstride) : Raw{};
-                }
-            };
-            // multiply out one nonzero and fold it into the running row sum;
-            // `vote`: every lane of the warp runs this step (uniform fast path)
-            auto step = [&](int row, float x, const Raw (&rw)[DA][C], bool vote) {
-                float part[C][VEC], fl[C][VEC];  // x * first D1-1 factors; last factor
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) part[c][v] = x;
-#pragma unroll
-                    for (int m = 0; m + 1 < D1; ++m) {
-                        float f[VEC];
-                        E::widen(rw[m][c], f);
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) part[c][v] *= f[v];
-                    }
-                    if (D1 > 0) E::widen(rw[DA - 1][c], fl[c]);
-                }
-                const bool ch = row != cur;
-                const bool any = vote ? __any_sync(FULL, ch) : ch;
-                if (any && ch) {
-                    if (cur >= 0) {
-                        if (MODE == M_ATOMIC) {
-                            write_row(cur, acc, true);
-                        } else if (!fclosed) {
-                            fclosed = true;
-                            frow = cur;
-#pragma unroll
-                            for (int c = 0; c < C; ++c)
-#pragma unroll
-                                for (int v = 0; v < VEC; ++v) facc[c][v] = acc[c][v];
-                        } else {
-                            write_row(cur, acc, false);  // row lies inside this group's block
-                        }
-                    }
-                    cur = row;
-#pragma unroll
-                    for (int c = 0; c < C; ++c)
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v)
-                            acc[c][v] = D1 > 0 ? part[c][v] * fl[c][v] : part[c][v];
-                } else {
-#pragma unroll
-                    for (int c = 0; c < C; ++c)
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v)
-                            acc[c][v] = D1 > 0 ? fmaf(part[c][v], fl[c][v], acc[c][v])
-                                               : acc[c][v] + part[c][v];
-                }
-            };
-
-            if (n == npw) {
-                // full chunk: every group walks exactly S nonzeros, U at a time
-                int t = 0;
-                for (; t + U <= S; t += U) {
-                    int rowu[U];
-                    float xu[U];
-                    Raw raw[U][DA][C];
-#pragma unroll
-                    for (int u = 0; u < U; ++u) fetch(e0 + t + u, rowu[u], xu[u], raw[u]);
-#pragma unroll
-                    for (int u = 0; u < U; ++u) step(rowu[u], xu[u], raw[u], true);
-                }
-                for (; t < S; ++t) {
-                    int row;
-                    float x;
-                    Raw rw[DA][C];
-                    fetch(e0 + t, row, x, rw);
-                    step(row, x, rw, true);
-                }
-            } else {
-                // the tensor's last, ragged chunk: groups hold different counts
-                for (int t = 0; t < cnt; ++t) {
-                    int row;
-                    float x;
-                    Raw rw[DA][C];
-                    fetch(e0 + t, row, x, rw);
-                    step(row, x, rw, false);
-                }
-            }
-
-            if (MODE == M_ATOMIC) {
-                if (cur >= 0) write_row(cur, acc, true);
-            } else {
-                // Segmented combine of the groups' open runs, in group order.
-                // Every lane tracks the running (orow, oacc) for its columns;
-                // group 0's lanes perform the writes.
-                float oacc[C][VEC];
-#pragma unroll
-                for (int c = 0; c < C; ++c)
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) oacc[c][v] = 0.0f;
-                int orow = -1;
-                const bool writer = (g == 0);
-                auto emit = [&](int row, float (&a)[C][VEC]) {
-                    if (writer) write_row(row, a, row == crow0 || row == crow1);
-                };
-                for (int g2 = 0; g2 < G; ++g2) {
-                    const int srcl = (g2 << log2L) | l;
-                    const int scur = __shfl_sync(FULL, cur, srcl);
-                    if (scur < 0) break;  // this and later groups got no nonzeros
-                    const int sfc = __shfl_sync(FULL, (int)fclosed, srcl);
-                    const int sfrow = __shfl_sync(FULL, frow, srcl);
-                    float F[C][VEC], A[C][VEC];
-#pragma unroll
-                    for (int c = 0; c < C; ++c)
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            F[c][v] = __shfl_sync(FULL, facc[c][v], srcl);
-                            A[c][v] = __shfl_sync(FULL, acc[c][v], srcl);
-                        }
-                    if (sfc) {
-                        if (orow == sfrow) {
-#pragma unroll
-                            for (int c = 0; c < C; ++c)
-#pragma unroll
-                                for (int v = 0; v < VEC; ++v) F[c][v] += oacc[c][v];
-                        } else if (orow >= 0) {
-                            emit(orow, oacc);
-                        }
-                        emit(sfrow, F);
-                        orow = scur;
-#pragma unroll
-                        for (int c = 0; c < C; ++c)
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v) oacc[c][v] = A[c][v];
-                    } else if (orow == scur) {
-#pragma unroll
-                        for (int c = 0; c < C; ++c)
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v) oacc[c][v] += A[c][v];
-                    } else {
-                        if (orow >= 0) emit(orow, oacc);
-                        orow = scur;
-#pragma unroll
-                        for (int c = 0; c < C; ++c)
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v) oacc[c][v] = A[c][v];
-                    }
-                }
-                if (orow >= 0) emit(orow, oacc);
-            }
-        }
+        mttkrp_chunk<FT, C, D1, MODE>(p, buf, n);
 
         __syncwarp();  // every lane is done with this stage before it is refilled
         if (lane == 0 && ch + 2 * nw < p.nchunks) {

@@ -1,0 +1,146 @@
+"""Build the learned selector's timing dataset and train it on the GPU.
+
+For each generated training tensor (order 3-5, Zipf skew 0-2, R 8-128,
+dims log-uniform in [1e2, 1e6], nnz log-uniform in [nnz_lo, nnz_hi]) and
+every mode, the exhaustive autotuner times all candidate schedules; the
+paper's Tab. "sizes" rule and the library's default rule are timed too.
+The network is trained on the first (1 - holdout) of the tensors with the
+library's own forward/backward/Adam kernels, and evaluated on the rest.
+
+    python -m paper_1809_09175_gb300.train_selector --count 500 --out DIR
+
+writes DIR/selector_dataset.npz, DIR/selector_weights.npz and
+DIR/selector_report.json.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+from . import binding as B  # noqa: E402
+from . import selector as S  # noqa: E402
+from .tensor import SparseTensor, factor_ld  # noqa: E402
+
+
+def device_factors(dims, R, fdt, seed):
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    ld = factor_ld(R)
+    out = []
+    for I in dims:
+        f = torch.zeros((I, ld), device="cuda")
+        f[:, :R] = torch.rand((I, R), generator=g, device="cuda")
+        out.append(f if fdt == "f32" else f.to(torch.bfloat16))
+    return out
+
+
+def measure_tensor(w, fdt, reps):
+    """Rows (features, candidate times, paper-rule time, default-rule time)."""
+    idx, vals = synth.coo_zipf_device(w.dims, w.nnz, w.s, w.seed)
+    T = SparseTensor(idx, vals, w.dims)
+    del idx, vals
+    T.build_permutation()
+    facs = device_factors(w.dims, w.R, fdt, w.seed)
+    ld = facs[0].shape[1]
+    ptrs = [f.data_ptr() for f in facs]
+    st = torch.cuda.current_stream().cuda_stream
+    rows = []
+    for n in range(T.order):
+        out = torch.empty((w.dims[n], ld), device="cuda")
+        feat = B.tensor_mode_features(T.handle, n, w.R, fdt)
+        _, _, times = B.mttkrp_autotune(T.handle, n, ptrs, fdt, w.R, ld, out.data_ptr(), reps, st)
+        paper = B.mttkrp_paper_schedule(w.R, fdt, "perm")
+        try:
+            t_paper = B.mttkrp_time_schedule(T.handle, n, ptrs, fdt, w.R, ld, out.data_ptr(), paper,
+                                             reps, st)
+        except B.SptError:  # the table's block does not fit this kernel's shared memory
+            paper.nnz_per_group = 32
+            t_paper = B.mttkrp_time_schedule(T.handle, n, ptrs, fdt, w.R, ld, out.data_ptr(), paper,
+                                             reps, st)
+        dflt = B.mttkrp_default_schedule(T.handle, n, fdt, w.R)
+        t_dflt = B.mttkrp_time_schedule(T.handle, n, ptrs, fdt, w.R, ld, out.data_ptr(), dflt, reps, st)
+        rows.append((np.array(feat, np.float32), np.array(times, np.float32), t_paper, t_dflt))
+        del out
+    T.close()
+    return rows
+
+
+def evaluate(pred, times, t_paper, t_dflt):
+    """Selected-candidate time vs the exhaustive best and the two rules."""
+    sel = []
+    for b in range(times.shape[0]):
+        v = times[b] > 0
+        y = np.where(v, pred[b], np.inf)
+        sel.append(times[b, int(np.argmin(y))])
+    sel = np.array(sel)
+    best = np.array([times[b][times[b] > 0].min() for b in range(times.shape[0])])
+    return {
+        "samples": int(times.shape[0]),
+        "total_ms_selected": float(sel.sum()),
+        "total_ms_best": float(best.sum()),
+        "total_ms_paper_rule": float(np.sum(t_paper)),
+        "total_ms_default_rule": float(np.sum(t_dflt)),
+        "regret_total": float(sel.sum() / best.sum() - 1.0),
+        "regret_mean": float(np.mean(sel / best - 1.0)),
+        "regret_p90": float(np.quantile(sel / best - 1.0, 0.9)),
+        "speedup_vs_paper_rule": float(np.sum(t_paper) / sel.sum()),
+        "speedup_vs_default_rule": float(np.sum(t_dflt) / sel.sum()),
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--count", type=int, default=500)
+    ap.add_argument("--nnz-lo", type=float, default=1e5)
+    ap.add_argument("--nnz-hi", type=float, default=1e7)
+    ap.add_argument("--holdout", type=float, default=0.1)
+    ap.add_argument("--epochs", type=int, default=4000)
+    ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--out", default=".")
+    a = ap.parse_args()
+    os.makedirs(a.out, exist_ok=True)
+    specs = synth.selector_specs(a.count, nnz_lo=a.nnz_lo, nnz_hi=a.nnz_hi)
+    X, TT, TP, TD, meta = [], [], [], [], []
+    t0 = time.time()
+    for i, w in enumerate(specs):
+        fdt = "bf16" if i % 2 else "f32"
+        for n, (f, t, tp, td) in enumerate(measure_tensor(w, fdt, a.reps)):
+            X.append(f); TT.append(t); TP.append(tp); TD.append(td)
+            meta.append((i, n, w.R, 0 if fdt == "f32" else 1, w.nnz, len(w.dims)))
+        if (i + 1) % 50 == 0:
+            print(f"{i + 1}/{len(specs)} tensors, {time.time() - t0:.0f} s", flush=True)
+    X = np.array(X, np.float32); TT = np.array(TT, np.float32)
+    TP = np.array(TP, np.float32); TD = np.array(TD, np.float32); meta = np.array(meta, np.int64)
+    np.savez(os.path.join(a.out, "selector_dataset.npz"), X=X, times=TT, t_paper=TP, t_default=TD,
+             meta=meta)
+    n_train_tensors = int(round(len(specs) * (1 - a.holdout)))
+    tr = meta[:, 0] < n_train_tensors
+    te = ~tr
+    mean, std = S.fit_scaling(X[tr])
+    net = S.Net.init(0, mean=mean, std=std)
+    T, M = S.targets(TT)
+    hist = net.train(X[tr], T[tr], M[tr], epochs=a.epochs, lr=3e-3, log_every=500)
+    net.save(os.path.join(a.out, "selector_weights.npz"))
+    rep = {"dataset_s": time.time() - t0, "tensors": len(specs), "samples": int(X.shape[0]),
+           "train_tensors": n_train_tensors, "loss": hist,
+           "train": evaluate(net.predict(X[tr]), TT[tr], TP[tr], TD[tr]),
+           "holdout": evaluate(net.predict(X[te]), TT[te], TP[te], TD[te])}
+    with open(os.path.join(a.out, "selector_report.json"), "w") as f:
+        json.dump(rep, f, indent=1)
+    print(json.dumps({k: rep[k] for k in ("tensors", "samples", "train", "holdout")}), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -275,3 +275,38 @@ def selector_specs(count: int = 500, seed0: int = 10_000, nnz_lo: float = 1e5,
         R = int(rng.integers(8, 129))
         out.append(Workload(f"sel{t}", dims, nnz, s, R, "uniform", seed0 + t))
     return out
+
+
+def coo_zipf_device(dims: Sequence[int], nnz: int, s, seed: int, device: str = "cuda"):
+    """The power-law COO recipe of :func:`coo_zipf`, drawn on the GPU with
+    torch's generator (a different random stream than the numpy one; used
+    where no oracle comparison is made, e.g. schedule-timing data).
+    Returns CUDA tensors (idx[d, nnz] int32, vals[nnz] float32)."""
+    import torch
+
+    d = len(dims)
+    ss = [float(s)] * d if np.isscalar(s) else [float(x) for x in s]
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    idx = torch.empty((d, nnz), dtype=torch.int32, device=device)
+    for m in range(d):
+        I = int(dims[m])
+        if I == 1:
+            idx[m].zero_()
+            continue
+        while True:
+            a = int(torch.randint(1, I, (1,), generator=g, device=device).item())
+            if math.gcd(a, I) == 1:
+                break
+        b = int(torch.randint(0, I, (1,), generator=g, device=device).item())
+        if ss[m] == 0.0:
+            r = torch.randint(0, I, (nnz,), generator=g, device=device, dtype=torch.int64)
+        else:
+            w = torch.arange(1, I + 1, dtype=torch.float64, device=device) ** (-ss[m])
+            cdf = torch.cumsum(w, 0)
+            cdf /= cdf[-1].clone()
+            u = torch.rand(nnz, generator=g, device=device, dtype=torch.float64)
+            r = torch.clamp(torch.searchsorted(cdf, u, right=True), max=I - 1)
+        idx[m] = ((a * r + b) % I).to(torch.int32)
+    vals = torch.rand(nnz, generator=g, device=device, dtype=torch.float32)
+    return idx, vals

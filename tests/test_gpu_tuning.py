@@ -1,0 +1,197 @@
+"""GPU tests: batched persistent MTTKRP, autotuner, selector network kernels.
+
+The batched launch is checked against the FP64 oracle and against the
+single-tensor entry point; the network's forward pass and gradients are
+checked against the FP64 oracle's; the trained selector (when its weights
+are present) is checked for what it gains over the fixed rules on tensors it
+was not trained on.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.gpu_util import rel_fro, to_device_factor, widen
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    import paper_1809_09175_gb300 as P
+    return P
+
+
+@pytest.mark.parametrize("fdt", ["f32", "bf16"])
+def test_batched_matches_oracle_and_single_launch(fdt):
+    P = _lib()
+    specs = synth.batched_specs(6, seed0=100, nnz_scale=0.02)
+    tensors, items, facs_all, outs_all, host = [], [], [], [], []
+    for w in specs:
+        idx, vals = w.coo()
+        T = P.SparseTensor(idx, vals, w.dims)
+        T.build_permutation()
+        facs_np = synth.factor_matrices(w.dims, w.R, w.seed, "uniform", dtype=fdt)
+        facs = [to_device_factor(f, fdt) for f in facs_np]
+        outs = [torch.full((I, facs[0].shape[1]), 5.0, device="cuda") for I in w.dims]
+        tensors.append(T); facs_all.append(facs); outs_all.append(outs)
+        host.append((idx, vals, facs_np))
+        items.append({"tensor": T.handle, "mode": -1, "rank": w.R, "ld": facs[0].shape[1],
+                      "factors": [f.data_ptr() for f in facs], "outs": [o.data_ptr() for o in outs]})
+    b, keep = P.mttkrp_batch_create(items, fdt)
+    ntask, nitem, blocks = P.mttkrp_batch_info(b)
+    assert ntask == sum(len(w.dims) for w in specs) and nitem > ntask and blocks > 0
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):  # captured once, replayed twice
+            P.mttkrp_batch_run(b, s.cuda_stream)
+    torch.cuda.synchronize()
+    P.mttkrp_batch_check(b)
+    for w, T, facs, outs, (idx, vals, facs_np) in zip(specs, tensors, facs_all, outs_all, host):
+        for n in range(len(w.dims)):
+            got = outs[n].cpu().numpy()
+            assert np.all(got[:, w.R:] == 0)
+            ref = oracle.mttkrp(idx, vals, w.dims, [widen(f, fdt, w.R) for f in facs_np], n, w.R)
+            assert rel_fro(got[:, :w.R], ref) <= 1e-5
+            single = T.mttkrp(n, facs, w.R).cpu().numpy()
+            assert rel_fro(got, single) <= 1e-6
+    P.mttkrp_batch_destroy(b)
+    for T in tensors:
+        T.close()
+
+
+def test_autotune_returns_fastest_valid_candidate():
+    P = _lib()
+    dims = (20000, 3000, 700)
+    idx, vals = synth.coo_zipf(dims, 300_000, 1.1, 3)
+    T = P.SparseTensor(idx, vals, dims)
+    T.build_permutation()
+    R = 24
+    facs = [torch.rand((I, 24), device="cuda") for I in dims]
+    out = torch.empty((dims[0], 24), device="cuda")
+    cands, valid = P.mttkrp_candidates(T.handle, 0, R)
+    assert len(cands) == P.SPT_NUM_CANDIDATES and sum(valid) >= 24
+    best, bms, times = P.mttkrp_autotune(T.handle, 0, [f.data_ptr() for f in facs], "f32", R, 24,
+                                         out.data_ptr(), 2)
+    times = np.array(times)
+    assert np.all((times > 0) == np.array(valid, bool))
+    assert abs(bms - times[times > 0].min()) < 1e-6
+    # the chosen schedule gives the right answer
+    ref = oracle.mttkrp(idx, vals, dims, [f.cpu().numpy()[:, :R].astype(np.float64) for f in facs], 0, R)
+    got = T.mttkrp(0, facs, R, sched=best).cpu().numpy()[:, :R]
+    assert rel_fro(got, ref) <= 1e-5
+    feat = np.array(P.tensor_mode_features(T.handle, 0, R, "f32"))
+    assert feat.shape == (P.SPT_NUM_FEATURES,) and np.isfinite(feat).all()
+    assert feat[0] == 3 and abs(feat[1] - np.log2(dims[0])) < 1e-5 and abs(feat[3] - np.log2(300_000)) < 1e-5
+    T.close()
+
+
+def _rand_net(F, H1, H2, K, seed):
+    rng = np.random.default_rng(seed)
+    ps = [rng.standard_normal((H1, F)) * 0.5, rng.standard_normal(H1) * 0.1,
+          rng.standard_normal((H2, H1)) * 0.3, rng.standard_normal(H2) * 0.1,
+          rng.standard_normal((K, H2)) * 0.3, rng.standard_normal(K) * 0.1]
+    flat = np.concatenate([p.reshape(-1) for p in ps]).astype(np.float32)
+    return [p.astype(np.float32).astype(np.float64) for p in ps], flat
+
+
+def test_mlp_forward_and_gradients_match_oracle():
+    P = _lib()
+    F, H1, H2, K, Bn = 12, 64, 48, 36, 200
+    ps, flat = _rand_net(F, H1, H2, K, 0)
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((Bn, F)).astype(np.float32)
+    T = rng.standard_normal((Bn, K)).astype(np.float32)
+    M = (rng.random((Bn, K)) < 0.8).astype(np.float32)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    x, t, m, p = d(X), d(T), d(M), d(flat)
+    work = torch.empty(P.mlp_workspace_floats(Bn, F, H1, H2, K), device="cuda")
+    y = torch.empty((Bn, K), device="cuda")
+    P.mlp_forward(Bn, F, H1, H2, K, x.data_ptr(), p.data_ptr(), y.data_ptr(), work.data_ptr())
+    ref = oracle.mlp_forward(X, ps)
+    assert rel_fro(y.cpu().numpy(), ref) <= 1e-5
+    yi = torch.empty((3, K), device="cuda")
+    P.mlp_infer(3, F, H1, H2, K, x.data_ptr(), p.data_ptr(), yi.data_ptr())
+    assert rel_fro(yi.cpu().numpy(), ref[:3]) <= 1e-5
+    grads = torch.zeros(flat.size, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    P.mlp_loss_grad(Bn, F, H1, H2, K, x.data_ptr(), p.data_ptr(), t.data_ptr(), m.data_ptr(),
+                    grads.data_ptr(), loss.data_ptr(), work.data_ptr())
+    lref, gref = oracle.mlp_loss_grad(X, ps, T, M)
+    assert abs(float(loss.item()) - lref) <= 1e-5 * abs(lref)
+    gflat = np.concatenate([g.reshape(-1) for g in gref])
+    assert rel_fro(grads.cpu().numpy(), gflat) <= 1e-4
+
+
+def test_mlp_training_fits_a_smooth_target():
+    P = _lib()
+    import paper_1809_09175_gb300.selector as S
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((512, S.F)).astype(np.float32)
+    W = rng.standard_normal((S.F, S.K)) * 0.3
+    T = np.tanh(X @ W).astype(np.float32)
+    M = np.ones_like(T)
+    net = S.Net.init(1, mean=X.mean(0), std=X.std(0))
+    hist = net.train(X, T, M, epochs=1500, lr=3e-3, log_every=100)
+    assert hist[-1] < 0.1 * hist[0], hist
+    pred = net.predict(X[:16])
+    assert np.mean((pred - T[:16]) ** 2) < 0.2
+
+
+def test_select_returns_a_valid_candidate():
+    P = _lib()
+    import paper_1809_09175_gb300.selector as S
+    dims = (5000, 400, 300)
+    idx, vals = synth.coo_zipf(dims, 50_000, 0.9, 4)
+    T = P.SparseTensor(idx, vals, dims)
+    T.build_permutation(-1, index_only=True)  # sorted candidates become invalid
+    net = S.Net.init(2)
+    for n in range(3):
+        sched, pred = net.choose(T, n, 20, "f32")
+        cands, valid = P.mttkrp_candidates(T.handle, n, 20)
+        q = [c.as_dict() for c in cands].index(sched.as_dict())
+        assert valid[q] == 1 and sched.scatter != P.SPT_SCATTER_SORTED
+        assert np.isfinite(pred).all()
+    T.close()
+
+
+WEIGHTS = os.path.join(ROOT, "paper_1809_09175_gb300", "selector_weights.npz")
+
+
+@pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="selector not trained yet")
+def test_trained_selector_gains_over_fixed_rules_on_unseen_tensors():
+    """On tensors outside the training set, the selector's schedules run
+    within 10% of the exhaustive autotuner's and faster than the paper's
+    fixed Tab. "sizes" rule."""
+    P = _lib()
+    import paper_1809_09175_gb300.selector as S
+    from paper_1809_09175_gb300.train_selector import device_factors
+    net = S.Net.load(WEIGHTS)
+    specs = synth.selector_specs(6, seed0=777_000, nnz_lo=1e6, nnz_hi=5e6)
+    t_sel = t_best = t_paper = t_dflt = 0.0
+    for i, w in enumerate(specs):
+        fdt = "bf16" if i % 2 else "f32"
+        idx, vals = synth.coo_zipf_device(w.dims, w.nnz, w.s, w.seed)
+        T = P.SparseTensor(idx, vals, w.dims)
+        T.build_permutation()
+        facs = device_factors(w.dims, w.R, fdt, w.seed)
+        ld = facs[0].shape[1]
+        ptrs = [f.data_ptr() for f in facs]
+        for n in range(len(w.dims)):
+            out = torch.empty((w.dims[n], ld), device="cuda")
+            _, bms, times = P.mttkrp_autotune(T.handle, n, ptrs, fdt, w.R, ld, out.data_ptr(), 3)
+            sched, _ = net.choose(T, n, w.R, fdt)
+            t_sel += P.mttkrp_time_schedule(T.handle, n, ptrs, fdt, w.R, ld, out.data_ptr(), sched, 3)
+            t_best += bms
+            paper = P.mttkrp_paper_schedule(w.R, fdt, "perm")
+            t_paper += P.mttkrp_time_schedule(T.handle, n, ptrs, fdt, w.R, ld, out.data_ptr(), paper, 3)
+            dflt = P.mttkrp_default_schedule(T.handle, n, fdt, w.R)
+            t_dflt += P.mttkrp_time_schedule(T.handle, n, ptrs, fdt, w.R, ld, out.data_ptr(), dflt, 3)
+        T.close()
+    print(f"selected {t_sel:.2f} ms, exhaustive best {t_best:.2f} ms, paper rule {t_paper:.2f} ms, "
+          f"default rule {t_dflt:.2f} ms")
+    assert t_sel <= 1.10 * t_best
+    assert t_sel < t_paper
