@@ -47,6 +47,14 @@ def parse():
                     help="nonzeros of the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the variants / CP-ALS extras")
+    ap.add_argument("--rank", type=int, default=0, help="override the workload's rank")
+    ap.add_argument("--batched", type=int, default=0,
+                    help="instead: the N-tensor batch, every mode in one persistent launch")
+    ap.add_argument("--cpals", type=int, default=0,
+                    help="instead: N CP-ALS iterations of the workload under the learned selector, "
+                         "exhaustive autotune, default and paper schedules")
+    ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1809_09175_gb300",
+                                                       "selector_weights.npz"))
     return ap.parse_args()
 
 
@@ -214,6 +222,8 @@ def run_ours(args):
     import synth
 
     w = synth.workload(args.workload, args.scale)
+    if args.rank:
+        w = synth.Workload(w.name, w.dims, w.nnz, w.s, args.rank, w.factor_dist, w.seed, w.factor_dtype)
     if world > 1:  # an independent problem per rank (weak scaling, no collective)
         w = synth.Workload(w.name, w.dims, w.nnz, w.s, w.R, w.factor_dist, w.seed + rank,
                            w.factor_dtype)
@@ -426,9 +436,195 @@ def measure_extras(args, P, torch, w, T, idx, vals, facs_np, dtype, R, d, ld, ou
     return out
 
 
+def run_cpals(args):
+    """CP-ALS iterations (captured graphs) of one workload under four sources
+    of per-mode MTTKRP schedules; the tensor is coalesced (duplicates summed)."""
+    import torch
+    import oracle
+    import paper_1809_09175_gb300 as P
+    import paper_1809_09175_gb300.selector as S
+    import synth
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = synth.workload(args.workload, args.scale)
+    if args.rank:
+        w = synth.Workload(w.name, w.dims, w.nnz, w.s, args.rank, w.factor_dist, w.seed, w.factor_dtype)
+    fdt = args.dtype or w.factor_dtype
+    R, d = w.R, len(w.dims)
+    ld = P.factor_ld(R)
+    t0 = time.perf_counter()
+    idx_d, vals_d = synth.coo_zipf_device(w.dims, w.nnz, w.s, w.seed)
+    T = P.SparseTensor(idx_d, vals_d, w.dims, coalesce=True)
+    del idx_d, vals_d
+    torch.cuda.synchronize()
+    t_ingest = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    T.build_permutation()
+    torch.cuda.synchronize()
+    t_perm = time.perf_counter() - t0
+    facs_np = w.factors(R, fdt)
+    def fresh():
+        return [(torch.from_numpy(f).cuda() if fdt == "f32" else
+                 torch.from_numpy(f.view(np.int16)).cuda().view(torch.bfloat16)) for f in facs_np]
+    facs = fresh()
+    ptrs = [f.data_ptr() for f in facs]
+    st = torch.cuda.current_stream().cuda_stream
+    scheds = {"default": [P.mttkrp_default_schedule(T.handle, n, fdt, R) for n in range(d)],
+              "paper_rule": [P.mttkrp_paper_schedule(R, fdt, "perm") for n in range(d)]}
+    t0 = time.perf_counter()
+    auto, auto_ms = [], []
+    for n in range(d):
+        out = torch.empty((w.dims[n], ld), device="cuda")
+        best, bms, _ = P.mttkrp_autotune(T.handle, n, ptrs, fdt, R, ld, out.data_ptr(), 2, st)
+        auto.append(best)
+        auto_ms.append(bms)
+        del out
+    t_tune = time.perf_counter() - t0
+    scheds["exhaustive"] = auto
+    if os.path.exists(args.weights):
+        net = S.Net.load(args.weights)
+        t0 = time.perf_counter()
+        scheds["selector"] = [net.choose(T, n, R, fdt)[0] for n in range(d)]
+        t_select = time.perf_counter() - t0
+    else:
+        t_select = None
+    res = {}
+    side = torch.cuda.Stream()
+    for name, sc in scheds.items():
+        for n in range(d):
+            try:
+                P.tensor_set_schedule(T.handle, n, fdt, R, sc[n])
+            except P.SptError:
+                P.tensor_set_schedule(T.handle, n, fdt, R, None)
+        f = fresh()
+        lam = torch.zeros(R, dtype=torch.float64, device="cuda")
+        fit = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ws = T.cp_als_workspace(R, ld)
+        fits, ms = [], []
+        with torch.cuda.stream(side):
+            for it in range(args.cpals):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(side)
+                T.cp_als_step(f, R, lam, fit, ws)
+                e1.record(side)
+                side.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                fits.append(float(fit.item()))
+        P.cp_als_status(ws.data_ptr(), side.cuda_stream)
+        steady = ms[2:] if len(ms) > 4 else ms  # first replay includes graph capture
+        res[name] = {"ms_per_iter": float(np.median(steady)), "iter_per_s": 1e3 / float(np.median(steady)),
+                     "fit_first": fits[0], "fit_last": fits[-1],
+                     "fit_nondecreasing": bool(all(b >= a - 1e-6 for a, b in zip(fits, fits[1:])))}
+        del ws, f
+    line = {"metric": METRIC, "workload": w.name, "dims": w.dims, "nnz_generated": w.nnz,
+            "nnz_coalesced": T.nnz, "R": R, "factors": fdt, "iterations": args.cpals,
+            "ingest_coalesce_s": t_ingest, "permutation_s": t_perm, "autotune_s": t_tune,
+            "select_s": t_select, "autotune_best_ms_per_mode": auto_ms, "cp_als": res,
+            "schedules": {k: [s_.as_dict() for s_ in v] for k, v in scheds.items()}}
+    if "selector" in res:
+        line["selector_vs_exhaustive_time_ratio"] = (res["selector"]["ms_per_iter"] /
+                                                     res["exhaustive"]["ms_per_iter"])
+    print(json.dumps(line), flush=True)
+    T.close()
+
+
+def run_batched(args):
+    """The many-tensor batch (order 3-4, dims 1e3-1e6, nnz 1e4-5e6, Zipf s in
+    [0, 1.5), R in {16, 32, 64}): every mode of every tensor in one persistent
+    launch (captured graph), against one launch per (tensor, mode); schedules
+    from the autotuner."""
+    import torch
+    import paper_1809_09175_gb300 as P
+    import synth
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    fdt = args.dtype or "f32"
+    specs = synth.batched_specs(args.batched)
+    Ts, facs_all, outs_all, items, tuned = [], [], [], [], []
+    t0 = time.perf_counter()
+    for w in specs:
+        idx, vals = synth.coo_zipf_device(w.dims, w.nnz, w.s, w.seed)
+        T = P.SparseTensor(idx, vals, w.dims)
+        del idx, vals
+        T.build_permutation()
+        ld = P.factor_ld(w.R)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(w.seed)
+        facs = []
+        for I in w.dims:
+            f = torch.zeros((I, ld), device="cuda")
+            f[:, :w.R] = torch.rand((I, w.R), generator=g, device="cuda")
+            facs.append(f if fdt == "f32" else f.to(torch.bfloat16))
+        outs = [torch.empty((I, ld), device="cuda") for I in w.dims]
+        sc = []
+        for n in range(len(w.dims)):  # best schedule among the sorted-traversal candidates
+            cands, valid = P.mttkrp_candidates(T.handle, n, w.R)
+            best, bms = None, 1e30
+            for c, v in zip(cands, valid):
+                if not v or c.scatter != P.SPT_SCATTER_SORTED:
+                    continue
+                ms = P.mttkrp_time_schedule(T.handle, n, [f.data_ptr() for f in facs], fdt, w.R, ld,
+                                            outs[n].data_ptr(), c, 1)
+                if ms < bms:
+                    best, bms = c, ms
+            sc.append(best)
+        Ts.append(T); facs_all.append(facs); outs_all.append(outs); tuned.append(sc)
+        items.append({"tensor": T.handle, "mode": -1, "rank": w.R, "ld": ld,
+                      "factors": [f.data_ptr() for f in facs], "outs": [o.data_ptr() for o in outs],
+                      "scheds": sc})
+    setup_s = time.perf_counter() - t0
+    b, keep = P.mttkrp_batch_create(items, fdt)
+    ntask, nitem, blocks = P.mttkrp_batch_info(b)
+    side = torch.cuda.Stream()
+    units = sum(w.nnz * w.R * len(w.dims) for w in specs)
+    with torch.cuda.stream(side):
+        for _ in range(args.warmup):
+            P.mttkrp_batch_run(b, side.cuda_stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        for _ in range(args.steps):
+            P.mttkrp_batch_run(b, side.cuda_stream)
+        e1.record(side)
+    torch.cuda.synchronize()
+    P.mttkrp_batch_check(b)
+    batch_ms = e0.elapsed_time(e1) / args.steps
+    # one launch per (tensor, mode) with the same schedules
+    def singles():
+        for T, facs, outs, sc, w in zip(Ts, facs_all, outs_all, tuned, specs):
+            for n in range(len(w.dims)):
+                T.mttkrp(n, facs, w.R, out=outs[n], sched=sc[n])
+    for _ in range(args.warmup):
+        singles()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        singles()
+    e1.record()
+    torch.cuda.synchronize()
+    single_ms = e0.elapsed_time(e1) / args.steps
+    line = {"metric": METRIC, "workload": f"batched{len(specs)}", "tensors": len(specs),
+            "total_nnz": int(sum(w.nnz for w in specs)), "tasks": ntask, "work_items": nitem,
+            "persistent_ctas": blocks, "factors": fdt, "setup_s": setup_s,
+            "batched_ms": batch_ms, "batched_nnzR_per_s": units / (batch_ms / 1e3),
+            "per_task_launches_ms": single_ms, "per_task_nnzR_per_s": units / (single_ms / 1e3),
+            "speedup": single_ms / batch_ms, "launches_per_run": 2, "graph": True}
+    print(json.dumps(line), flush=True)
+    P.mttkrp_batch_destroy(b)
+    for T in Ts:
+        T.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.cpals:
+        run_cpals(a)
+    elif a.batched:
+        run_batched(a)
     else:
         run_ours(a)

@@ -190,6 +190,12 @@ spt_status mttkrp(spt_tensor t, int mode, const void *const *factors, spt_dtype 
                   int ld, const float *lambda, float *out, const spt_schedule *sched,
                   void *stream);
 
+/* Record the schedule to use for (mode, fdt, rank) wherever no schedule is
+ * passed (mttkrp with sched == NULL, cp_als_step), e.g. one chosen by
+ * mttkrp_autotune or mttkrp_select.  s == NULL clears it.  The schedule is
+ * validated now (SPT_EINVAL / SPT_ESTATE as for mttkrp). */
+spt_status tensor_set_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank, const spt_schedule *s);
+
 /* The schedule mttkrp() runs for sched == NULL (host logic, no launch). */
 spt_status mttkrp_default_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank,
                                    spt_schedule *out);

@@ -94,6 +94,7 @@ _sig("tensor_get_permutation", _vp, C.c_int, _vp, _vp)
 _sig("mttkrp", _vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _vp, _vp,
      C.POINTER(spt_schedule), _vp)
 _sig("mttkrp_default_schedule", _vp, C.c_int, C.c_int, C.c_int, C.POINTER(spt_schedule))
+_sig("tensor_set_schedule", _vp, C.c_int, C.c_int, C.c_int, C.POINTER(spt_schedule))
 _sig("mttkrp_paper_sizes", C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int))
 _sig("mttkrp_paper_schedule", C.c_int, C.c_int, C.c_int, C.POINTER(spt_schedule))
 _sig("spt_stream_copy", _vp, _vp, C.c_size_t, _vp)
@@ -102,7 +103,7 @@ _sig("spt_convert_f32", _vp, _vp, C.c_int, C.c_int64, _vp)
 EXPORTED = ["spt_last_error", "spt_device_info", "tensor_create_coo", "tensor_destroy",
             "tensor_info", "tensor_get_coo", "tensor_norm2", "tensor_check",
             "build_mode_permutation", "tensor_get_permutation", "mttkrp",
-            "mttkrp_default_schedule", "mttkrp_paper_sizes", "mttkrp_paper_schedule",
+            "mttkrp_default_schedule", "tensor_set_schedule", "mttkrp_paper_sizes", "mttkrp_paper_schedule",
             "spt_stream_copy", "spt_convert_f32"]
 
 
@@ -229,6 +230,10 @@ def mttkrp_default_schedule(t: int, mode: int, fdt, rank: int) -> spt_schedule:
     s = spt_schedule()
     _chk(_L.mttkrp_default_schedule(t, mode, _dt(fdt), rank, C.byref(s)))
     return s
+
+
+def tensor_set_schedule(t: int, mode: int, fdt, rank: int, sched: Optional[spt_schedule]):
+    _chk(_L.tensor_set_schedule(t, mode, _dt(fdt), rank, C.byref(sched) if sched is not None else None))
 
 
 def mttkrp_paper_sizes(rank: int):

@@ -261,6 +261,20 @@ spt_status mttkrp(spt_tensor t, int mode, const void *const *factors, spt_dtype 
     return launch_mttkrp(t, mode, factors, fdt, rank, ld, lambda, out, s, (cudaStream_t)stream);
 }
 
+spt_status tensor_set_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank, const spt_schedule *s) {
+    if (!t) return fail(SPT_EINVAL, "tensor_set_schedule: NULL tensor");
+    if (mode < 0 || mode >= t->d || rank < 1) return fail(SPT_EINVAL, "tensor_set_schedule: bad mode/rank");
+    drop_graphs(t);
+    if (!s) { t->pref_set[mode] = false; return SPT_OK; }
+    spt_status c = check_schedule(t, mode, fdt, rank, *s);
+    if (c) return c;
+    t->pref_set[mode] = true;
+    t->pref_rank[mode] = rank;
+    t->pref_fdt[mode] = fdt;
+    t->pref[mode] = *s;
+    return SPT_OK;
+}
+
 spt_status mttkrp_default_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank,
                                    spt_schedule *out) {
     if (!t || !out) return fail(SPT_EINVAL, "mttkrp_default_schedule: NULL argument");

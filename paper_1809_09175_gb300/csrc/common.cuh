@@ -48,6 +48,12 @@ struct spt_tensor_s {
     int32_t *perm[SPT_MAX_ORDER] = {nullptr};
     void *sorted_buf[SPT_MAX_ORDER] = {nullptr};
     ModeStats stats[SPT_MAX_ORDER];
+    // schedule chosen for a mode (by the autotuner or the selector) for one
+    // (rank, dtype); used where the caller passes no schedule
+    bool pref_set[SPT_MAX_ORDER] = {false};
+    int pref_rank[SPT_MAX_ORDER] = {0};
+    spt_dtype pref_fdt[SPT_MAX_ORDER] = {SPT_F32};
+    spt_schedule pref[SPT_MAX_ORDER];
     int *dev_err = nullptr;  // device status word for kernels of this tensor
 };
 

@@ -43,6 +43,9 @@ spt_status ensure_smem_attr(MttkrpKernelFn fn, int smem) {
 }  // namespace
 
 spt_schedule default_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank) {
+    if (t->pref_set[mode] && t->pref_rank[mode] == rank && t->pref_fdt[mode] == fdt &&
+        check_schedule(t, mode, fdt, rank, t->pref[mode]) == SPT_OK)
+        return t->pref[mode];
     spt_schedule s{};
     s.scatter = t->sorted_buf[mode] ? SPT_SCATTER_SORTED
                                     : (t->perm[mode] ? SPT_SCATTER_PERM : SPT_SCATTER_ATOMIC);
