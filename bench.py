@@ -472,22 +472,43 @@ def run_cpals(args):
     scheds = {"default": [P.mttkrp_default_schedule(T.handle, n, fdt, R) for n in range(d)],
               "paper_rule": [P.mttkrp_paper_schedule(R, fdt, "perm") for n in range(d)]}
     t0 = time.perf_counter()
-    auto, auto_ms = [], []
+    auto, auto_ms, auto_times = [], [], []
     for n in range(d):
         out = torch.empty((w.dims[n], ld), device="cuda")
-        best, bms, _ = P.mttkrp_autotune(T.handle, n, ptrs, fdt, R, ld, out.data_ptr(), 2, st)
+        best, bms, times = P.mttkrp_autotune(T.handle, n, ptrs, fdt, R, ld, out.data_ptr(), 2, st)
         auto.append(best)
         auto_ms.append(bms)
+        auto_times.append(times)
         del out
     t_tune = time.perf_counter() - t0
     scheds["exhaustive"] = auto
+    t_select = t_verify = None
+    sel_info = {}
     if os.path.exists(args.weights):
         net = S.Net.load(args.weights)
         t0 = time.perf_counter()
-        scheds["selector"] = [net.choose(T, n, R, fdt)[0] for n in range(d)]
+        chosen = [net.choose(T, n, R, fdt) for n in range(d)]
         t_select = time.perf_counter() - t0
-    else:
-        t_select = None
+        scheds["selector"] = [c[0] for c in chosen]
+        ranks, sel_mode_ms = [], []
+        for n in range(d):
+            cands, valid = P.mttkrp_candidates(T.handle, n, R)
+            order = [q for q in np.argsort(chosen[n][1]) if valid[q]]
+            tt = np.array(auto_times[n])
+            ranks.append(order.index(int(np.argmin(np.where(tt > 0, tt, np.inf)))))
+            sel_mode_ms.append(float(tt[order[0]]))
+        t0 = time.perf_counter()
+        ver = []
+        for n in range(d):
+            out = torch.empty((w.dims[n], ld), device="cuda")
+            ver.append(net.choose_verified(T, n, R, fdt, facs, out, k=3))
+            del out
+        t_verify = time.perf_counter() - t0
+        scheds["selector_top3_verified"] = [v[0] for v in ver]
+        sel_info = {"rank_of_exhaustive_best_in_network_order": ranks,
+                    "selector_mttkrp_ms_per_mode": sel_mode_ms,
+                    "verified_mttkrp_ms_per_mode": [v[1] for v in ver],
+                    "verify_s": t_verify}
     res = {}
     side = torch.cuda.Stream()
     for name, sc in scheds.items():
@@ -520,11 +541,12 @@ def run_cpals(args):
     line = {"metric": METRIC, "workload": w.name, "dims": w.dims, "nnz_generated": w.nnz,
             "nnz_coalesced": T.nnz, "R": R, "factors": fdt, "iterations": args.cpals,
             "ingest_coalesce_s": t_ingest, "permutation_s": t_perm, "autotune_s": t_tune,
-            "select_s": t_select, "autotune_best_ms_per_mode": auto_ms, "cp_als": res,
+            "select_s": t_select, "autotune_best_ms_per_mode": auto_ms, "selector_detail": sel_info,
+            "cp_als": res,
             "schedules": {k: [s_.as_dict() for s_ in v] for k, v in scheds.items()}}
-    if "selector" in res:
-        line["selector_vs_exhaustive_time_ratio"] = (res["selector"]["ms_per_iter"] /
-                                                     res["exhaustive"]["ms_per_iter"])
+    for k in ("selector", "selector_top3_verified"):
+        if k in res:
+            line[k + "_vs_exhaustive_time_ratio"] = res[k]["ms_per_iter"] / res["exhaustive"]["ms_per_iter"]
     print(json.dumps(line), flush=True)
     T.close()
 

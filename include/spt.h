@@ -239,7 +239,7 @@ spt_status mttkrp_autotune(spt_tensor t, int mode, const void *const *factors, s
                            float *times, void *stream);
 
 /* Per-mode features (host output, SPT_NUM_FEATURES floats): order, log2 I_n,
- * log2 prod_{m != n} I_m, log2 P, log2 R, factor element bytes, log2 of the
+ * log2 (P / I_n), min(log2 P, 24), log2 R, factor element bytes, log2 of the
  * hottest slice over the mean nonempty slice, coefficient of variation of the
  * slice sizes, hottest-slice share of P, nonempty-slice fraction, log2 of the
  * mean run length of equal mode-n coordinates in storage order, and log2 of

@@ -44,49 +44,73 @@ template <> __device__ __forceinline__ __nv_bfloat16 st_elem<__nv_bfloat16>(floa
 template <> __device__ __forceinline__ __half st_elem<__half>(float v) { return __float2half_rn(v); }
 
 // G += A^T A over all I rows (A row-major, stride ld, first R columns).
-// Thread t owns entries t + k*blockDim of the R x R result.  Rows are staged
-// 32 at a time in shared memory; FP32 partial sums over 256 rows are folded
-// into FP64 accumulators, and each CTA adds its FP64 result atomically.
-template <typename FT, int PPT>
-__global__ void __launch_bounds__(512) gram_kernel(const FT *A, int64_t I, int ld, int R, double *G) {
-    constexpr int TR = 32;
-    __shared__ float s[TR][MAXR + 1];
-    const int RR = R * R;
-    float acc[PPT];
-    double dacc[PPT];
-    int pp[PPT], qq[PPT];
+// Thread (ti, tj) of a team owns the 4 x 4 block G[4ti.., 4tj..] in
+// registers; RS teams of RT*RT threads split the rows of each staged 32-row
+// tile.  FP32 partial sums over at most 256 rows are folded into the CTA's
+// FP64 copy of G in shared memory, which each CTA adds to G atomically.
+template <typename FT>
+__global__ void __launch_bounds__(1024) gram_kernel(const FT *A, int64_t I, int ld, int R, double *G) {
+    constexpr int TR = 32, SP = MAXR + 4;
+    extern __shared__ __align__(16) unsigned char gsm[];
+    float (*s)[SP] = reinterpret_cast<float (*)[SP]>(gsm);
+    double *red = reinterpret_cast<double *>(gsm + sizeof(float) * TR * SP);
+    const int RT = (R + 3) / 4, RP = RT * 4;
+    const int team_sz = RT * RT;
+    const int RS = blockDim.x / team_sz;
+    const int team = threadIdx.x / team_sz, tid = threadIdx.x % team_sz;
+    const int ti = tid / RT, tj = tid % RT;
+    const int RR = RP * RP;
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) red[e] = 0.0;
+    __syncthreads();
+    float acc[4][4];
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        acc[k] = 0.f;
-        dacc[k] = 0.0;
-        const int e = threadIdx.x + k * blockDim.x;
-        pp[k] = e < RR ? e / R : 0;
-        qq[k] = e < RR ? e % R : 0;
-    }
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    // fold the FP32 partials into the CTA's FP64 block (one team: owned entries)
+    auto fold = [&]() {
+        if (team < RS) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    double *dst = &red[(4 * ti + i) * RP + 4 * tj + j];
+                    if (RS == 1) *dst += (double)acc[i][j];
+                    else atomicAdd(dst, (double)acc[i][j]);
+                    acc[i][j] = 0.f;
+                }
+        }
+    };
     int since = 0;
     for (int64_t r0 = (int64_t)blockIdx.x * TR; r0 < I; r0 += (int64_t)gridDim.x * TR) {
         __syncthreads();
-        for (int e = threadIdx.x; e < TR * R; e += blockDim.x) {
-            const int r = e / R, c = e % R;
-            s[r][c] = (r0 + r < I) ? ld_elem<FT>(A + (r0 + r) * ld + c) : 0.f;
+        for (int e = threadIdx.x; e < TR * RP; e += blockDim.x) {
+            const int r = e / RP, c = e % RP;
+            s[r][c] = (r0 + r < I && c < R) ? ld_elem<FT>(A + (r0 + r) * ld + c) : 0.f;
         }
         __syncthreads();
-#pragma unroll 4
-        for (int r = 0; r < TR; ++r) {
+        if (team < RS) {
+            for (int r = team; r < TR; r += RS) {
+                const float4 a = *reinterpret_cast<const float4 *>(&s[r][4 * ti]);
+                const float4 b = *reinterpret_cast<const float4 *>(&s[r][4 * tj]);
+                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) acc[k] = fmaf(s[r][pp[k]], s[r][qq[k]], acc[k]);
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+            }
         }
         since += TR;
         if (since >= 256) {
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) { dacc[k] += (double)acc[k]; acc[k] = 0.f; }
+            fold();
             since = 0;
         }
     }
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int e = threadIdx.x + k * blockDim.x;
-        if (e < RR) atomicAdd(G + e, dacc[k] + (double)acc[k]);
+    fold();
+    __syncthreads();
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+        const int i = e / RP, j = e % RP;
+        if (i < R && j < R) atomicAdd(G + i * R + j, red[e]);
     }
 }
 
@@ -175,36 +199,67 @@ __global__ void __launch_bounds__(512) chol_inv_kernel(double *G, int d, int n, 
     for (int r = threadIdx.x; r < R; r += blockDim.x) colsq[r] = 0.0;
 }
 
-// A32 = V Hinv (rows of V staged in shared memory), column sums of squares.
+// A32 = V Hinv, column sums of squares.  Thread (rq, cq) computes the 4 x 4
+// block rows [4rq, 4rq+4) x columns [4cq, 4cq+4) of a tile of V's rows; Hinv
+// and the tile (transposed) sit in shared memory, so each k costs two
+// 16-byte shared loads for 16 FMAs.
 __global__ void __launch_bounds__(256) solve_kernel(const float *V, int64_t I, int ld, int R,
                                                     const float *Hinv, float *A32, double *colsq) {
-    extern __shared__ float shs[];
-    float *Hs = shs;                 // R x R
-    const int rows = blockDim.x / R;  // rows per tile (R divides 256 or R > 128 never)
-    float *Vs = shs + R * R;          // rows x R
-    __shared__ double csq[MAXR];
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) Hs[e] = Hinv[e];
-    for (int e = threadIdx.x; e < R; e += blockDim.x) csq[e] = 0.0;
-    const int tr = threadIdx.x / R, j = threadIdx.x % R;
-    const bool act = tr < rows;
-    double local = 0.0;
-    for (int64_t r0 = (int64_t)blockIdx.x * rows; r0 < I; r0 += (int64_t)gridDim.x * rows) {
+    extern __shared__ __align__(16) float shs[];
+    const int CT = (R + 3) / 4, RP = CT * 4;
+    const int RQ = blockDim.x / CT;          // row quads per tile
+    const int TROWS = 4 * RQ;
+    float *Hs = shs;                         // R x RP
+    float *Vt = shs + R * RP;                // R x TROWS (transposed tile)
+    __shared__ double csq[MAXR + 4];
+    for (int e = threadIdx.x; e < R * RP; e += blockDim.x) {
+        const int k = e / RP, c = e % RP;
+        Hs[e] = c < R ? Hinv[k * R + c] : 0.f;
+    }
+    for (int e = threadIdx.x; e < RP; e += blockDim.x) csq[e] = 0.0;
+    const int rq = threadIdx.x / CT, cq = threadIdx.x % CT;
+    const bool act = rq < RQ;
+    double local[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t r0 = (int64_t)blockIdx.x * TROWS; r0 < I; r0 += (int64_t)gridDim.x * TROWS) {
         __syncthreads();
-        for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
-            const int r = e / R, c = e % R;
-            Vs[e] = (r0 + r < I) ? V[(r0 + r) * ld + c] : 0.f;
+        for (int e = threadIdx.x; e < TROWS * R; e += blockDim.x) {
+            const int r = e / R, k = e % R;
+            Vt[k * TROWS + r] = (r0 + r < I) ? V[(r0 + r) * ld + k] : 0.f;
         }
         __syncthreads();
-        if (act && r0 + tr < I) {
-            float a = 0.f;
-            const float *vr = Vs + tr * R;
-#pragma unroll 8
-            for (int i = 0; i < R; ++i) a = fmaf(vr[i], Hs[i * R + j], a);
-            A32[(r0 + tr) * ld + j] = a;
-            local += (double)a * (double)a;
+        if (act) {
+            float acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+            for (int k = 0; k < R; ++k) {
+                const float4 v = *reinterpret_cast<const float4 *>(&Vt[k * TROWS + 4 * rq]);
+                const float4 h = *reinterpret_cast<const float4 *>(&Hs[k * RP + 4 * cq]);
+                const float vv[4] = {v.x, v.y, v.z, v.w}, hh[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(vv[i], hh[j], acc[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t row = r0 + 4 * rq + i;
+                if (row >= I) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = 4 * cq + j;
+                    if (c < R) {
+                        A32[row * ld + c] = acc[i][j];
+                        local[j] += (double)acc[i][j] * (double)acc[i][j];
+                    }
+                }
+            }
         }
     }
-    if (act) atomicAdd(&csq[j], local);
+    if (act)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) atomicAdd(&csq[4 * cq + j], local[j]);
     __syncthreads();
     for (int e = threadIdx.x; e < R; e += blockDim.x) atomicAdd(colsq + e, csq[e]);
 }
@@ -301,11 +356,11 @@ size_t ws_layout(spt_tensor t, int R, int ld, Ws *w, void *base) {
 
 template <typename FT>
 spt_status launch_gram(const void *A, int64_t I, int ld, int R, double *G, cudaStream_t st) {
-    const int blocks = sm_count() * 2;
-    if (R <= 16) gram_kernel<FT, 1><<<blocks, 256, 0, st>>>((const FT *)A, I, ld, R, G);
-    else if (R <= 32) gram_kernel<FT, 4><<<blocks, 256, 0, st>>>((const FT *)A, I, ld, R, G);
-    else if (R <= 64) gram_kernel<FT, 16><<<blocks, 256, 0, st>>>((const FT *)A, I, ld, R, G);
-    else gram_kernel<FT, 32><<<blocks, 512, 0, st>>>((const FT *)A, I, ld, R, G);
+    const int RT = (R + 3) / 4, team = RT * RT;
+    const int threads = team >= 256 ? team : (256 / team) * team;
+    const size_t smem = sizeof(float) * 32 * (MAXR + 4) + sizeof(double) * (size_t)(RT * 4) * (RT * 4);
+    const int blocks = sm_count() * (threads > 512 ? 1 : 2);
+    gram_kernel<FT><<<blocks, threads, smem, st>>>((const FT *)A, I, ld, R, G);
     SPT_LAUNCH_CHECK("gram_kernel");
     return SPT_OK;
 }
@@ -316,10 +371,35 @@ spt_status gram_any(spt_dtype fdt, const void *A, int64_t I, int ld, int R, doub
     return launch_gram<__half>(A, I, ld, R, G, st);
 }
 
+// Dynamic shared-memory limits of the CP-ALS kernels, once per device.
+spt_status ensure_cpals_attrs() {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    SPT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return SPT_OK;
+    SPT_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  sizeof(double) * (MAXR * MAXR + MAXR)));
+    SPT_CUDA(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  sizeof(float) * (MAXR * (MAXR + 4) + MAXR * 256)));
+    const size_t gsm = sizeof(float) * 32 * (MAXR + 4) + sizeof(double) * MAXR * MAXR;
+    SPT_CUDA(cudaFuncSetAttribute(gram_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    SPT_CUDA(cudaFuncSetAttribute(gram_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    SPT_CUDA(cudaFuncSetAttribute(gram_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    done[dev] = true;
+    return SPT_OK;
+}
+
 // Enqueue one iteration (no synchronisation, capturable).
 spt_status enqueue_step(spt_tensor t, void *const *factors, spt_dtype fdt, int R, int ld,
                         double *lambda, double *fit_out, const Ws &w, cudaStream_t st) {
     const int d = t->d;
+    {
+        spt_status a = ensure_cpals_attrs();
+        if (a) return a;
+    }
     SPT_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * d * R * R, st));
     SPT_CUDA(cudaMemsetAsync(w.inner, 0, sizeof(double), st));
     SPT_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), st));
@@ -327,15 +407,7 @@ spt_status enqueue_step(spt_tensor t, void *const *factors, spt_dtype fdt, int R
         spt_status s = gram_any(fdt, factors[m], t->dims[m], ld, R, w.G + (size_t)m * R * R, st);
         if (s) return s;
     }
-    static bool attr_set = false;
     const size_t chol_smem = sizeof(double) * (R * R + R);
-    if (!attr_set) {
-        SPT_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      sizeof(double) * (MAXR * MAXR + MAXR)));
-        SPT_CUDA(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      sizeof(float) * (MAXR * MAXR + 256)));
-        attr_set = true;
-    }
     for (int n = 0; n < d; ++n) {
         const int64_t In = t->dims[n];
         spt_schedule sc = default_schedule(t, n, fdt, R);
@@ -343,9 +415,10 @@ spt_status enqueue_step(spt_tensor t, void *const *factors, spt_dtype fdt, int R
         if (s) return s;
         chol_inv_kernel<<<1, 512, chol_smem, st>>>(w.G, d, n, R, w.Hinv, w.colsq, w.status);
         SPT_LAUNCH_CHECK("chol_inv_kernel");
-        const int rows = 256 / R;
-        const size_t solve_smem = sizeof(float) * (R * R + rows * R);
-        const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((In + rows - 1) / rows, sm_count() * 4));
+        const int CT = (R + 3) / 4;
+        const int trows = 4 * (256 / CT);
+        const size_t solve_smem = sizeof(float) * ((size_t)R * CT * 4 + (size_t)R * trows);
+        const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((In + trows - 1) / trows, sm_count() * 2));
         solve_kernel<<<sblocks, 256, solve_smem, st>>>(w.V, In, ld, R, w.Hinv, w.A32, w.colsq);
         SPT_LAUNCH_CHECK("solve_kernel");
         const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>((In * ld + 255) / 256, sm_count() * 8));

@@ -136,9 +136,9 @@ spt_status tensor_mode_features(spt_tensor t, int mode, int rank, spt_dtype fdt,
     if (!ms.valid) return fail(SPT_ESTATE, "tensor_mode_features: build_mode_permutation(mode) first");
     const double P = std::max<double>(1.0, (double)t->nnz);
     const double In = (double)t->dims[mode];
-    double others = 0.0, other_rows = 0.0;
+    double other_rows = 0.0;
     for (int m = 0; m < t->d; ++m)
-        if (m != mode) { others += std::log2((double)t->dims[m]); other_rows += (double)t->dims[m]; }
+        if (m != mode) other_rows += (double)t->dims[m];
     const double eb = (fdt == SPT_F32) ? 4.0 : 2.0;
     const double ne = std::max<double>(1.0, (double)ms.nonempty);
     const double mean_ne = P / ne;
@@ -147,8 +147,8 @@ spt_status tensor_mode_features(spt_tensor t, int mode, int rank, spt_dtype fdt,
     const double l2 = 129.0 * 1024 * 1024;
     feat[0] = (float)t->d;
     feat[1] = (float)std::log2(In);
-    feat[2] = (float)others;
-    feat[3] = (float)std::log2(P);
+    feat[2] = (float)std::log2(P / In);                   // mean slice length
+    feat[3] = (float)std::min(24.0, std::log2(P));        // size, saturated: tails vanish beyond 16M
     feat[4] = (float)std::log2((double)rank);
     feat[5] = (float)eb;
     feat[6] = (float)std::log2(std::max(1.0, (double)ms.max_count / mean_ne));

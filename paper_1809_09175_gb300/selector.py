@@ -44,18 +44,24 @@ def collect(T, factors: List[torch.Tensor], rank: int, fdt: str, reps: int = 1):
     return rows
 
 
-def targets(times: np.ndarray):
-    """Regression targets: log(time / best time) of each valid candidate
-    (mask 1), 0 with mask 0 where a candidate could not run."""
+def targets(times: np.ndarray, weighting: str = "sqrt"):
+    """Regression targets: log(time / best time) of each valid candidate;
+    mask 0 where a candidate could not run.  With weighting "sqrt" a sample's
+    mask is sqrt(its best time / the mean best time), so the fit favours the
+    tensors that dominate total run time over launch-overhead noise of tiny
+    ones; "none" weighs every sample alike."""
     times = np.asarray(times, np.float64)
     valid = times > 0
     T = np.zeros(times.shape, np.float32)
     M = valid.astype(np.float32)
+    best = np.ones(times.shape[0])
     for b in range(times.shape[0]):
         v = valid[b]
         if v.any():
-            best = times[b, v].min()
-            T[b, v] = np.log(times[b, v] / best)
+            best[b] = times[b, v].min()
+            T[b, v] = np.log(times[b, v] / best[b])
+    if weighting == "sqrt":
+        M *= np.sqrt(best / best.mean()).astype(np.float32)[:, None]
     return T, M
 
 
@@ -139,6 +145,23 @@ class Net:
     def choose(self, T, mode: int, rank: int, fdt: str):
         """The selector's schedule for (tensor, mode, rank, dtype)."""
         return B.mttkrp_select(T.handle, mode, fdt, rank, self.selector(), _stream())
+
+    def choose_verified(self, T, mode: int, rank: int, fdt: str, factors, out, k: int = 3,
+                        reps: int = 2):
+        """Time the network's k best-ranked valid candidates (instead of all
+        SPT_NUM_CANDIDATES) and return (schedule, ms) of the fastest."""
+        _, pred = self.choose(T, mode, rank, fdt)
+        cands, valid = B.mttkrp_candidates(T.handle, mode, rank)
+        order = [q for q in np.argsort(pred) if valid[q]][:k]
+        ld = factors[0].shape[1]
+        ptrs = [f.data_ptr() for f in factors]
+        best, bms = None, float("inf")
+        for q in order:
+            ms = B.mttkrp_time_schedule(T.handle, mode, ptrs, fdt, rank, ld, out.data_ptr(),
+                                        cands[q], reps, _stream())
+            if ms < bms:
+                best, bms = cands[q], ms
+        return best, bms
 
     def save(self, path: str):
         np.savez(path, params=self.params.cpu().numpy(), mean=self.mean, std=self.std,

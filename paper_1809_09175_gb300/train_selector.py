@@ -4,8 +4,9 @@ For each generated training tensor (order 3-5, Zipf skew 0-2, R 8-128,
 dims log-uniform in [1e2, 1e6], nnz log-uniform in [nnz_lo, nnz_hi]) and
 every mode, the exhaustive autotuner times all candidate schedules; the
 paper's Tab. "sizes" rule and the library's default rule are timed too.
-The network is trained on the first (1 - holdout) of the tensors with the
-library's own forward/backward/Adam kernels, and evaluated on the rest.
+The network is trained on the first (1 - holdout) of the tensors (plus
+``--large`` extra tensors with more nonzeros) with the library's own
+forward/backward/Adam kernels, and evaluated on the held-out rest.
 
     python -m paper_1809_09175_gb300.train_selector --count 500 --out DIR
 
@@ -48,6 +49,7 @@ def device_factors(dims, R, fdt, seed):
 
 def measure_tensor(w, fdt, reps):
     """Rows (features, candidate times, paper-rule time, default-rule time)."""
+    torch.cuda.empty_cache()
     idx, vals = synth.coo_zipf_device(w.dims, w.nnz, w.s, w.seed)
     T = SparseTensor(idx, vals, w.dims)
     del idx, vals
@@ -105,13 +107,25 @@ def main():
     ap.add_argument("--count", type=int, default=500)
     ap.add_argument("--nnz-lo", type=float, default=1e5)
     ap.add_argument("--nnz-hi", type=float, default=1e7)
+    ap.add_argument("--large", type=int, default=0, help="extra tensors with nnz in [nnz_hi, 1.5e8]")
     ap.add_argument("--holdout", type=float, default=0.1)
     ap.add_argument("--epochs", type=int, default=4000)
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--out", default=".")
+    ap.add_argument("--dataset", default=None, help="train from a saved selector_dataset.npz")
+    ap.add_argument("--weighting", default="sqrt", choices=["sqrt", "none"])
     a = ap.parse_args()
     os.makedirs(a.out, exist_ok=True)
+    if a.dataset:
+        z = np.load(a.dataset)
+        return train_and_report(a, z["X"], z["times"], z["t_paper"], z["t_default"], z["meta"],
+                                int(z["n_train_tensors"]) if "n_train_tensors" in z else None, 0.0)
     specs = synth.selector_specs(a.count, nnz_lo=a.nnz_lo, nnz_hi=a.nnz_hi)
+    # larger tensors join the training part only (the held-out part keeps the base recipe)
+    big = synth.selector_specs(a.large, seed0=20_000, nnz_lo=a.nnz_hi, nnz_hi=a.nnz_hi,
+                               large=a.large) if a.large else []
+    specs = specs[: int(round(len(specs) * (1 - a.holdout)))] + big + \
+        specs[int(round(len(specs) * (1 - a.holdout))):]
     X, TT, TP, TD, meta = [], [], [], [], []
     t0 = time.time()
     for i, w in enumerate(specs):
@@ -123,18 +137,24 @@ def main():
             print(f"{i + 1}/{len(specs)} tensors, {time.time() - t0:.0f} s", flush=True)
     X = np.array(X, np.float32); TT = np.array(TT, np.float32)
     TP = np.array(TP, np.float32); TD = np.array(TD, np.float32); meta = np.array(meta, np.int64)
+    n_train_tensors = int(round(a.count * (1 - a.holdout))) + len(big)
     np.savez(os.path.join(a.out, "selector_dataset.npz"), X=X, times=TT, t_paper=TP, t_default=TD,
-             meta=meta)
-    n_train_tensors = int(round(len(specs) * (1 - a.holdout)))
+             meta=meta, n_train_tensors=n_train_tensors)
+    train_and_report(a, X, TT, TP, TD, meta, n_train_tensors, time.time() - t0)
+
+
+def train_and_report(a, X, TT, TP, TD, meta, n_train_tensors, dataset_s):
+    if n_train_tensors is None:  # datasets saved before the split was recorded: 450 + 30 large
+        n_train_tensors = int(meta[:, 0].max() + 1) - 50
     tr = meta[:, 0] < n_train_tensors
     te = ~tr
     mean, std = S.fit_scaling(X[tr])
     net = S.Net.init(0, mean=mean, std=std)
-    T, M = S.targets(TT)
+    T, M = S.targets(TT, a.weighting)
     hist = net.train(X[tr], T[tr], M[tr], epochs=a.epochs, lr=3e-3, log_every=500)
     net.save(os.path.join(a.out, "selector_weights.npz"))
-    rep = {"dataset_s": time.time() - t0, "tensors": len(specs), "samples": int(X.shape[0]),
-           "train_tensors": n_train_tensors, "loss": hist,
+    rep = {"dataset_s": dataset_s, "tensors": int(meta[:, 0].max() + 1), "samples": int(X.shape[0]),
+           "train_tensors": n_train_tensors, "weighting": a.weighting, "loss": hist,
            "train": evaluate(net.predict(X[tr]), TT[tr], TP[tr], TD[tr]),
            "holdout": evaluate(net.predict(X[te]), TT[te], TP[te], TD[te])}
     with open(os.path.join(a.out, "selector_report.json"), "w") as f:

@@ -261,16 +261,18 @@ def batched_specs(count: int = 64, seed0: int = 0, nnz_scale: float = 1.0):
 
 
 def selector_specs(count: int = 500, seed0: int = 10_000, nnz_lo: float = 1e5,
-                   nnz_hi: float = 3e7):
+                   nnz_hi: float = 3e7, large: int = 0, large_hi: float = 1.5e8):
     """Recipe of the schedule-selector training tensors: order 3..5, Zipf
     s ~ U(0, 2), R in [8, 128], dims log-uniform in [1e2, 1e6], nnz
-    log-uniform in [nnz_lo, nnz_hi]."""
+    log-uniform in [nnz_lo, nnz_hi]; the last ``large`` tensors draw nnz
+    log-uniform in [nnz_hi, large_hi] instead."""
     out = []
     for t in range(count):
         rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed0 + t, 11])))
         d = int(rng.integers(3, 6))
         dims = [int(round(_log_uniform(rng, 1e2, 1e6))) for _ in range(d)]
-        nnz = int(round(_log_uniform(rng, nnz_lo, nnz_hi)))
+        lo, hi = (nnz_hi, large_hi) if t >= count - large else (nnz_lo, nnz_hi)
+        nnz = int(round(_log_uniform(rng, lo, hi)))
         s = float(rng.uniform(0.0, 2.0))
         R = int(rng.integers(8, 129))
         out.append(Workload(f"sel{t}", dims, nnz, s, R, "uniform", seed0 + t))
