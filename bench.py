@@ -131,6 +131,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def kernel_traffic(nnz):
+    """DRAM bytes per MTTKRP launch from the committed ncu capture, scaled to
+    `nnz` nonzeros (the 16-byte nonzero record is ~3/4 of the traffic and
+    grows with nnz), or None when the kernel sources changed since."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic_mttkrp_kernel_sorted_zipf3d_2e7nnz_R16.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for ln in open(p):
+        if ":" in ln and not ln.startswith("#"):
+            k, v = ln.split(":", 1)
+            kv[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for f in ("mttkrp_kernel.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1809_09175_gb300", "csrc", f), "rb").read())
+    if kv.get("kernel_source_sha256") != h.hexdigest():
+        return None
+    return float(kv["bytes_per_nonzero"]) * nnz
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -224,9 +245,10 @@ def run_ours(args):
     w = synth.workload(args.workload, args.scale)
     if args.rank:
         w = synth.Workload(w.name, w.dims, w.nnz, w.s, args.rank, w.factor_dist, w.seed, w.factor_dtype)
-    if world > 1:  # an independent problem per rank (weak scaling, no collective)
-        w = synth.Workload(w.name, w.dims, w.nnz, w.s, w.R, w.factor_dist, w.seed + rank,
-                           w.factor_dtype)
+    from paper_1809_09175_gb300 import multi
+    if world > 1:  # an independent problem per rank (weak scaling, no data-path collective)
+        w = synth.Workload(w.name, w.dims, w.nnz, w.s, w.R, w.factor_dist,
+                           multi.rank_seed(w.seed, rank), w.factor_dtype)
     dtype = args.dtype or w.factor_dtype
     R = w.R
     d = len(w.dims)
@@ -285,15 +307,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     T.check()
-    total_ms = t0.elapsed_time(t1)
+    local_ms = t0.elapsed_time(t1)
+    units = w.nnz * R * d  # per step, this rank
+    # slowest rank's time, all ranks' units (timing reductions only)
+    total_ms, all_units = multi.reduce_timing(local_ms, units * args.steps, device="cuda")
     if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
         dist.barrier()
     ms_step = total_ms / args.steps
-    units = w.nnz * R * d
-    value = units * world / (ms_step / 1e3)
+    value = all_units / (total_ms / 1e3)
     mode_ms = [sum(ev[k][n][0].elapsed_time(ev[k][n][1]) for k in range(args.steps)) / args.steps
                for n in range(d)]
 
@@ -350,7 +371,9 @@ def run_ours(args):
         "per_mode_nnzR_per_s": [w.nnz * R / (m / 1e3) for m in mode_ms],
         "roofline": {"bound": "hbm", "kernel": "mttkrp_kernel", "achieved": achieved,
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                     "peak_kind": peak_kind, "traffic": None,
+                     "peak_kind": peak_kind,
+                     "traffic": (kernel_traffic(w.nnz) if args.scatter == "sorted" and dtype == "f32"
+                                 and R == 16 and d == 3 else None),
                      "compulsory_GBps": comp_gbs, "compulsory_frac": comp_gbs / hbm_peak},
         "gpu_launches": d * args.steps,
         "ingest_s": ingest_s, "permutation_s": perm_s,
@@ -561,8 +584,11 @@ def run_batched(args):
     import synth
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_1809_09175_gb300 import multi
     fdt = args.dtype or "f32"
-    specs = synth.batched_specs(args.batched)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    specs = multi.shard(synth.batched_specs(args.batched), rank, world)
     Ts, facs_all, outs_all, items, tuned = [], [], [], [], []
     t0 = time.perf_counter()
     for w in specs:
