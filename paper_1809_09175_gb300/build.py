@@ -38,10 +38,11 @@ def _compile(src, extra):
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
+    extra = list(extra) + os.environ.get("SPT_NVCC_DEFINES", "").split()
+    if not force and not extra and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    extra = list(extra) + (["-Xptxas", "-v"] if verbose else [])
+    extra = extra + (["-Xptxas", "-v"] if verbose else [])
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         results = list(ex.map(lambda s: _compile(s, extra), srcs))

@@ -49,17 +49,24 @@ __device__ __forceinline__ int find_task(const BatchTask *tasks, int ntasks, int
     return lo;
 }
 
+template <typename FT, int C, int D1>
+__device__ __forceinline__ void run_chunk(const MttkrpParams &p, const int32_t *buf, int n) {
+    int b0, b1;
+    chunk_bounds<D1, M_SORTED>(p, buf, n, b0, b1);
+    mttkrp_chunk<FT, C, D1, M_SORTED>(p, buf, n, b0, b1, nullptr);
+}
+
 template <typename FT>
 __device__ __forceinline__ void run_item(const MttkrpParams &p, int d1, int C, const int32_t *buf, int n) {
     switch (d1 * 2 + C - 1) {
-    case 2: mttkrp_chunk<FT, 1, 1, M_SORTED>(p, buf, n); break;
-    case 3: mttkrp_chunk<FT, 2, 1, M_SORTED>(p, buf, n); break;
-    case 4: mttkrp_chunk<FT, 1, 2, M_SORTED>(p, buf, n); break;
-    case 5: mttkrp_chunk<FT, 2, 2, M_SORTED>(p, buf, n); break;
-    case 6: mttkrp_chunk<FT, 1, 3, M_SORTED>(p, buf, n); break;
-    case 7: mttkrp_chunk<FT, 2, 3, M_SORTED>(p, buf, n); break;
-    case 8: mttkrp_chunk<FT, 1, 4, M_SORTED>(p, buf, n); break;
-    case 9: mttkrp_chunk<FT, 2, 4, M_SORTED>(p, buf, n); break;
+    case 2: run_chunk<FT, 1, 1>(p, buf, n); break;
+    case 3: run_chunk<FT, 2, 1>(p, buf, n); break;
+    case 4: run_chunk<FT, 1, 2>(p, buf, n); break;
+    case 5: run_chunk<FT, 2, 2>(p, buf, n); break;
+    case 6: run_chunk<FT, 1, 3>(p, buf, n); break;
+    case 7: run_chunk<FT, 2, 3>(p, buf, n); break;
+    case 8: run_chunk<FT, 1, 4>(p, buf, n); break;
+    case 9: run_chunk<FT, 2, 4>(p, buf, n); break;
     default: break;
     }
 }

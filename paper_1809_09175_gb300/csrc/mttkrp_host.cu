@@ -55,11 +55,11 @@ spt_schedule default_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank) {
     while (lanes < need && lanes < 32) lanes <<= 1;
     s.lanes_per_nnz = lanes;
     s.chunks = need > 32 ? 2 : 1;
-    // staging of about 7 KB per warp (two stages of the d+1 arrays), so four
-    // 8-warp CTAs fit an SM's shared memory; at most 256 nonzeros per chunk
+    // about 7 KB of shared memory per warp (two staging buffers plus the run
+    // carry), so four 8-warp CTAs fit an SM; at most 256 nonzeros per chunk
     const int narr = s.scatter == SPT_SCATTER_PERM ? 1
                      : (s.scatter == SPT_SCATTER_SORTED ? record_words(t->d) : t->d + 1);
-    const int npw = std::min(256, 896 / narr);
+    const int npw = std::min(256, (7168 - 16 - carry_bytes(s.chunks, lanes)) / (8 * narr));
     s.nnz_per_group = std::max(4, npw / (32 / lanes));
     s.warps_per_cta = 8;
     s.ctas_per_sm = 0;
@@ -126,7 +126,7 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
     p.err = t->dev_err;
 
     const int wpe = kmode == M_PERM ? 1 : (kmode == M_SORTED ? record_words(t->d) : D1 + 2);
-    const size_t smem = 16 * (size_t)wpc + (size_t)wpc * 2 * wpe * npw * 4;
+    const size_t smem = 16 * (size_t)wpc + (size_t)wpc * carry_bytes(C, L) + (size_t)wpc * 2 * wpe * npw * 4;
     if (smem > 227 * 1024)
         return fail(SPT_EINVAL, "schedule: staging buffers exceed 227 KB of shared memory "
                                 "(lower warps_per_cta or nnz_per_group)");

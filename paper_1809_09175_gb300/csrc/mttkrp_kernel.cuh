@@ -4,8 +4,8 @@
 //
 // Work decomposition (GB300 mapping of the paper's league/team/vector levels,
 // Sec. 3 Tab. "Levels of Parallelism"):
-//  * A warp owns a chunk of `npw` consecutive nonzeros of the traversal order
-//    (persistent grid, chunks dealt round-robin to warps).  The chunk's
+//  * Each warp of a persistent grid owns a contiguous range of chunks of
+//    `npw` consecutive nonzeros of the traversal order.  A chunk's
 //    nonzeros are staged into the warp's shared memory with 1-D bulk copies
 //    (cp.async.bulk, mbarrier completion), double buffered, so the next chunk
 //    streams in while this one is computed.
@@ -29,9 +29,10 @@
 //                For both, a group writes a finished row with a plain store;
 //                the first and last run of every group are combined across
 //                the warp with shuffles (a segmented reduction over the
-//                groups), and only the chunk's first and last row are added
-//                atomically, because only those rows can be shared with other
-//                warps.
+//                groups), and the last open run is carried in registers into
+//                the warp's next chunk, so only the first and last row of the
+//                warp's whole range are added atomically: only those rows can
+//                be shared with other warps.
 //  * Columns: rank block rb covers columns [rb*L*C*VEC, ...); lane l's chunk
 //    c starts at column rb*L*C*VEC + (c*L + l)*VEC.  Columns >= R are
 //    computed from the factors' padding and written as zeros.
@@ -79,14 +80,46 @@ __device__ __forceinline__ void red_add4(float *dst, const float *v) {
 }
 
 // Register cap: small column blocks fit two 512-thread CTAs (<= 64 registers).
+#ifndef SPT_MTTKRP_MINBLOCKS
+#define SPT_MTTKRP_MINBLOCKS 2
+#endif
 template <typename FT, int C> struct MinBlocks {
-    static constexpr int value = (Elem<FT>::VEC * C <= 4) ? 2 : 1;
+    static constexpr int value = (Elem<FT>::VEC * C <= 4) ? SPT_MTTKRP_MINBLOCKS : 1;
 };
+
+// Open row sum carried from one chunk to the next by a warp that walks a
+// contiguous range of chunks (one rank block), kept in the warp's shared
+// memory between chunks: a 16-byte header (the carried row, then the first
+// and last row of the warp's range) and C x 4 floats for each of the L column
+// slices (every group holds the same slices).
+__host__ __device__ constexpr int carry_bytes(int C, int L) { return 16 + 16 * C * L; }
+
+// First and last mode-n coordinate of the staged chunk.
+template <int D1, int MODE>
+__device__ __forceinline__ void chunk_bounds(const MttkrpParams &p, const int32_t *buf, int n, int &b0,
+                                             int &b1) {
+    constexpr int REC = record_words(D1 + 1);
+    if (MODE == M_SORTED) {
+        b0 = buf[0];
+        b1 = buf[(n - 1) * REC];
+    } else if (MODE == M_PERM) {
+        b0 = __ldg(p.rows + buf[0]);
+        b1 = __ldg(p.rows + buf[n - 1]);
+    } else {
+        b0 = b1 = -1;
+    }
+}
 
 // Compute one staged chunk of n nonzeros (n <= npw) for every rank block:
 // gather, multiply, segmented accumulate and write (see the file comment).
+// Rows b0 and b1 may be shared with other warps and are added atomically;
+// every other finished row is stored.  With `carry` (single rank block), the
+// chunk's last open run is handed over instead of written, the carried run of
+// the previous chunk joins this chunk's first run, and the shared rows are the
+// range's first and last rows from the carry header.
 template <typename FT, int C, int D1, int MODE>
-__device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_t *buf, int n) {
+__device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_t *buf, int n, int b0,
+                                             int b1, unsigned char *carry) {
     using E = Elem<FT>;
     using Raw = typename E::Raw;
     constexpr int VEC = E::VEC;
@@ -107,14 +140,6 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
 
     const int e0 = g * S;
     const int cnt = max(0, min(S, n - e0));
-    int crow0 = 0, crow1 = 0;
-    if (MODE == M_SORTED) {
-        crow0 = buf[0];
-        crow1 = buf[(n - 1) * REC];
-    } else if (MODE == M_PERM) {
-        crow0 = __ldg(p.rows + buf[0]);
-        crow1 = __ldg(p.rows + buf[n - 1]);
-    }
 
     for (int rb = 0; rb < p.n_rb; ++rb) {
         int col[C], nv[C];
@@ -287,15 +312,20 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
             // Segmented combine of the groups' open runs, in group order.
             // Every lane tracks the running (orow, oacc) for its columns;
             // group 0's lanes perform the writes.
+            int *crow_p = reinterpret_cast<int *>(carry);
+            float *cacc_p = carry ? reinterpret_cast<float *>(carry + 16) + l * (C * VEC) : nullptr;
             float oacc[C][VEC];
 #pragma unroll
             for (int c = 0; c < C; ++c)
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) oacc[c][v] = 0.0f;
-            int orow = -1;
+                for (int v = 0; v < VEC; ++v) oacc[c][v] = carry ? cacc_p[c * VEC + v] : 0.0f;
+            int orow = carry ? *crow_p : -1;
             const bool writer = (g == 0);
             auto emit = [&](int row, float (&a)[C][VEC]) {
-                if (writer) write_row(row, a, row == crow0 || row == crow1);
+                if (writer) {
+                    const int s0 = carry ? crow_p[1] : b0, s1 = carry ? crow_p[2] : b1;
+                    write_row(row, a, row == s0 || row == s1);
+                }
             };
             for (int g2 = 0; g2 < G; ++g2) {
                 const int srcl = (g2 << log2L) | l;
@@ -340,10 +370,45 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
                         for (int v = 0; v < VEC; ++v) oacc[c][v] = A[c][v];
                 }
             }
-            if (orow >= 0) emit(orow, oacc);
+            if (carry) {
+                __syncwarp();  // every lane has read the carry
+                if (lane == 0) *crow_p = orow;
+                if (g == 0) {
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) cacc_p[c * VEC + v] = oacc[c][v];
+                }
+            } else if (orow >= 0) {
+                emit(orow, oacc);
+            }
         }
     }
+}
 
+// Atomically add a carried row sum (rank block 0) to the output.
+template <typename FT, int C>
+__device__ __forceinline__ void flush_carry(const MttkrpParams &p, const unsigned char *carry) {
+    constexpr int VEC = Elem<FT>::VEC;
+    const int lane = threadIdx.x & 31;
+    const int L = 1 << p.log2L;
+    const int row = *reinterpret_cast<const int *>(carry);
+    if ((lane >> p.log2L) != 0 || row < 0) return;  // group 0 writes
+    const int l = lane & (L - 1);
+    const float *acc = reinterpret_cast<const float *>(carry + 16) + l * (C * VEC);
+    float *dst = p.out + (int64_t)row * p.old;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const int col = (c * L + l) * VEC;
+        const int nv = max(0, min(VEC, p.R - col));
+        if (nv == 0) continue;
+        float w[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v)
+            w[v] = v < nv ? acc[c * VEC + v] * (p.lambda ? __ldg(p.lambda + col + v) : 1.0f) : 0.0f;
+#pragma unroll
+        for (int q = 0; q < VEC; q += 4) red_add4(dst + col + q, w + q);
+    }
 }
 
 template <typename FT, int C, int D1, int MODE>
@@ -359,11 +424,17 @@ __global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(co
     const int wpc = blockDim.x >> 5;
     const int npw = p.npw;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw) + 2 * warp;
-    int32_t *wbuf = reinterpret_cast<int32_t *>(smem_raw + 16 * wpc) + (size_t)warp * 2 * WPE * npw;
+    const int cb = carry_bytes(C, 1 << p.log2L);
+    unsigned char *carry = smem_raw + 16 * wpc + (size_t)warp * cb;
+    int32_t *wbuf = reinterpret_cast<int32_t *>(smem_raw + 16 * wpc + (size_t)wpc * cb) +
+                    (size_t)warp * 2 * WPE * npw;
 
-    const int64_t gw = (int64_t)blockIdx.x * wpc + warp;
-    const int64_t nw = (int64_t)gridDim.x * wpc;
-    if (gw >= p.nchunks) return;  // whole warp idle (warp-uniform)
+    // each warp walks a contiguous range of chunks
+    const int gw = blockIdx.x * wpc + warp;
+    const int nw = gridDim.x * wpc;
+    const int ch_begin = (int)((int64_t)gw * p.nchunks / nw);
+    const int ch_end = (int)((int64_t)(gw + 1) * p.nchunks / nw);
+    if (ch_begin >= ch_end) return;  // whole warp idle (warp-uniform)
 
     const int32_t *src[NARR];
     if (MODE == M_PERM) {
@@ -383,13 +454,13 @@ __global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(co
     }
     __syncwarp();
 
-    auto chunk_len = [&](int64_t ch) {
-        const int64_t c0 = ch * npw;
+    auto chunk_len = [&](int ch) {
+        const int64_t c0 = (int64_t)ch * npw;
         return (int)(p.nnz - c0 < (int64_t)npw ? p.nnz - c0 : (int64_t)npw);
     };
     // lane 0: stage the 16-byte-aligned body of chunk `ch` into stage `s`
-    auto issue = [&](int64_t ch, int s) {
-        const int64_t c0 = ch * npw;
+    auto issue = [&](int ch, int s) {
+        const int64_t c0 = (int64_t)ch * npw;
         const int n = chunk_len(ch);
         int32_t *buf = wbuf + s * WPE * npw;
         if (MODE == M_SORTED) {
@@ -406,24 +477,49 @@ __global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(co
         }
     };
     if (lane == 0) {
-        issue(gw, 0);
-        if (gw + nw < p.nchunks) issue(gw + nw, 1);
+        issue(ch_begin, 0);
+        if (ch_begin + 1 < ch_end) issue(ch_begin + 1, 1);
+    }
+
+    // Sorted traversals with one rank block carry the open run across the
+    // range's chunks; only the range's first and last rows are then shared.
+    const bool use_carry = (MODE != M_ATOMIC) && p.n_rb == 1;
+    if (use_carry) {
+        const int64_t e_first = (int64_t)ch_begin * npw;
+        const int64_t e_last = ((int64_t)ch_end * npw < p.nnz ? (int64_t)ch_end * npw : p.nnz) - 1;
+        if (lane == 0) {
+            int *hdr = reinterpret_cast<int *>(carry);
+            hdr[0] = -1;
+            if (MODE == M_SORTED) {
+                hdr[1] = __ldg(p.rec + e_first * REC);
+                hdr[2] = __ldg(p.rec + e_last * REC);
+            } else {
+                hdr[1] = __ldg(p.rows + __ldg(p.perm + e_first));
+                hdr[2] = __ldg(p.rows + __ldg(p.perm + e_last));
+            }
+        }
+        if ((lane >> p.log2L) == 0) {
+            float *ca = reinterpret_cast<float *>(carry + 16) + lane * (C * Elem<FT>::VEC);
+#pragma unroll
+            for (int q = 0; q < C * Elem<FT>::VEC; ++q) ca[q] = 0.0f;
+        }
+        __syncwarp();
     }
 
     int k = 0;
-    for (int64_t ch = gw; ch < p.nchunks; ch += nw, ++k) {
+    for (int ch = ch_begin; ch < ch_end; ++ch, ++k) {
         const int s = k & 1;
         const uint32_t parity = (uint32_t)(k >> 1) & 1u;
         const bool ok = mbar_wait(&bars[s], parity);
         if (!__all_sync(FULL, ok)) {
             // bounded-wait budget spent: report, let copies in flight land, leave
             if (lane == 0) atomicExch(p.err, SPT_DEV_TIMEOUT);
-            if (ch + nw < p.nchunks) mbar_wait(&bars[s ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
+            if (ch + 1 < ch_end) mbar_wait(&bars[s ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
             mbar_wait(&bars[s], parity);
             return;
         }
         int32_t *buf = wbuf + s * WPE * npw;
-        const int64_t c0 = ch * npw;
+        const int64_t c0 = (int64_t)ch * npw;
         const int n = chunk_len(ch);
         if (MODE == M_SORTED) {  // words past the 16-byte body of a ragged chunk
             const int W = n * REC, wb = W & ~3;
@@ -437,13 +533,23 @@ __global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(co
         }
         __syncwarp();
 
-        mttkrp_chunk<FT, C, D1, MODE>(p, buf, n);
+        if (use_carry) {
+            mttkrp_chunk<FT, C, D1, MODE>(p, buf, n, -1, -1, carry);
+        } else {
+            int b0, b1;
+            chunk_bounds<D1, MODE>(p, buf, n, b0, b1);
+            mttkrp_chunk<FT, C, D1, MODE>(p, buf, n, b0, b1, nullptr);
+        }
 
         __syncwarp();  // every lane is done with this stage before it is refilled
-        if (lane == 0 && ch + 2 * nw < p.nchunks) {
+        if (lane == 0 && ch + 2 < ch_end) {
             fence_proxy_async_smem();
-            issue(ch + 2 * nw, s);
+            issue(ch + 2, s);
         }
+    }
+    if (use_carry) {
+        __syncwarp();
+        flush_carry<FT, C>(p, carry);
     }
 }
 

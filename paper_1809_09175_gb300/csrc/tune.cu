@@ -49,7 +49,8 @@ static size_t sched_smem(spt_tensor t, const spt_schedule &s) {
     const int npw = G * S;
     const int wpe = s.scatter == SPT_SCATTER_PERM ? 1
                     : (s.scatter == SPT_SCATTER_SORTED ? record_words(t->d) : t->d + 1);
-    return 16 * (size_t)s.warps_per_cta + (size_t)s.warps_per_cta * 2 * wpe * npw * 4;
+    return 16 * (size_t)s.warps_per_cta + (size_t)s.warps_per_cta * carry_bytes(s.chunks, s.lanes_per_nnz) +
+           (size_t)s.warps_per_cta * 2 * wpe * npw * 4;
 }
 
 bool candidate_valid(spt_tensor t, int mode, int rank, const spt_schedule &s, int q) {
