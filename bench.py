@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="zipf3d_1e6x5e5x2e5_nnz1e8")
     ap.add_argument("--dtype", default=None, help="factor storage (default: the workload's)")
-    ap.add_argument("--scatter", default="sorted", choices=["atomic", "perm", "sorted"])
+    ap.add_argument("--scatter", default="sorted", choices=["atomic", "perm", "sorted", "private"])
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (debug only)")
     ap.add_argument("--cpu-sample", type=int, default=4_000_000,
                     help="nonzeros of the oracle's bounded CPU sample")
@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--cpals", type=int, default=0,
                     help="instead: N CP-ALS iterations of the workload under the learned selector, "
                          "exhaustive autotune, default and paper schedules")
+    ap.add_argument("--paper-sweep", action="store_true",
+                    help="instead: the paper's 30K x 40K x 50K / 1e7-nonzero tensor, MTTKRP for R = 8..256 "
+                         "step 8 with fp64, fp32 and bf16 factors, and 10 CP-ALS iterations at R = 128")
+    ap.add_argument("--sweep-ranks", default="8:257:8", help="start:stop:step of the rank sweep")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1809_09175_gb300",
                                                        "selector_weights.npz"))
     return ap.parse_args()
@@ -400,13 +404,19 @@ def measure_extras(args, P, torch, w, T, idx, vals, facs_np, dtype, R, d, ld, ou
     for fdt in ["f32", "bf16"]:
         fnp = w.factors(R, fdt)
         fd = [_dev_factor(torch, f, fdt) for f in fnp]
-        for sc in (["sorted"] if args.scatter != "perm" else []) + ["perm", "atomic"]:
+        for sc in (["sorted"] if args.scatter != "perm" else []) + ["perm", "atomic", "private"]:
             ms = []
             for n in range(d):
                 s = sched_for(n, sc, fdt)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
-                T.mttkrp(n, fd, R, out=outs[n], sched=s)
+                try:
+                    T.mttkrp(n, fd, R, out=outs[n], sched=s)
+                except P.SptError:  # private: this mode's output copy does not fit a cluster
+                    if sc != "private":
+                        raise
+                    ms.append(None)
+                    continue
                 e0.record(stream)
                 for _ in range(3):
                     T.mttkrp(n, fd, R, out=outs[n], sched=s)
@@ -416,15 +426,19 @@ def measure_extras(args, P, torch, w, T, idx, vals, facs_np, dtype, R, d, ld, ou
             # sampled-row error against the oracle (same stored factor values)
             errs = []
             A64 = [oracle.as_f64(f, fdt)[:, :R].copy() for f in fnp]
-            if sc == "sorted" or sc == "atomic":
+            if sc in ("sorted", "atomic", "private"):
                 for n in range(d):
+                    if ms[n] is None:
+                        errs.append(None)
+                        continue
                     rows = sampled_rows(w, idx, n, R)
                     T.mttkrp(n, fd, R, out=outs[n], sched=sched_for(n, sc, fdt))
                     got = outs[n][torch.from_numpy(rows).long().cuda(), :R].double().cpu().numpy()
                     ref = oracle.mttkrp_rows(idx, vals, w.dims, A64, n, R, rows)
                     errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+            ran = [m for m in ms if m is not None]
             var[f"{sc}/{fdt}"] = {"ms_per_mode": ms,
-                                  "nnzR_per_s": w.nnz * R * d / (sum(ms) / 1e3),
+                                  "nnzR_per_s": w.nnz * R * len(ran) / (sum(ran) / 1e3) if ran else None,
                                   "rel_err_sampled_rows": errs or None}
         del fd
     out["variants"] = var
@@ -666,10 +680,133 @@ def run_batched(args):
         T.close()
 
 
+def run_paper_sweep(args):
+    """The paper's synthetic study (Sec. 7): MTTKRP of every mode of the
+    30K x 40K x 50K tensor with 1e7 uniformly random nonzeros for R = 8..256
+    in steps of 8, in the sorted (Fig. MTTKRP-C) and atomic (Fig. MTTKRP-B)
+    traversals, with fp64 (the paper's precision), fp32 and bf16 factors;
+    then 10 CP-ALS iterations at R = 128 (the paper's speed-up experiment).
+    Reported per point: nnz*R/s, the paper's bandwidth model
+    ((d R + 3) s_r + d s_o) P / t over the measured copy bandwidth, and for
+    fp64 the fp64 operations (d per nonzero and column) over the measured
+    fp64 FMA rate."""
+    import torch
+    import oracle
+    import paper_1809_09175_gb300 as P
+    import synth
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = synth.workload("uniform3d_30kx40kx50k_nnz1e7", args.scale)
+    d = len(w.dims)
+    idx, vals = w.coo()
+    T = P.SparseTensor(idx, vals, w.dims)
+    T.build_permutation()
+    st = torch.cuda.current_stream()
+    peak_gbs, peak_kind = measured_peaks()
+
+    def ev_time(fn, reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        fn()
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # fp64 / fp32 FMA throughput of this device (the fp64 path's roofline)
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    fma = {}
+    for dt, iters in (("f64", 1 << 13), ("f32", 1 << 16)):
+        flops = P.spt_fma_probe(dt, iters, sink.data_ptr(), st.cuda_stream)
+        fma[dt] = flops / (ev_time(lambda: P.spt_fma_probe(dt, iters, sink.data_ptr(), st.cuda_stream), 3) / 1e3)
+
+    a, b, c = (int(x) for x in args.sweep_ranks.split(":"))
+    s_o = 4
+    rows = []
+    g = torch.Generator(device="cuda")
+    for R in range(a, b, c):
+        ld = P.factor_ld(R)
+        for dt in ("f64", "f32", "bf16"):
+            g.manual_seed(R)
+            facs = []
+            for I in w.dims:
+                f = torch.zeros((I, ld), dtype=torch.float64, device="cuda")
+                f[:, :R] = torch.rand((I, R), generator=g, dtype=torch.float64, device="cuda")
+                facs.append(f.to({"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dt]))
+            out = torch.empty((max(w.dims), ld), device="cuda",
+                              dtype=torch.float64 if dt == "f64" else torch.float32)
+            s_r = {"f64": 8, "f32": 4, "bf16": 2}[dt]
+            for sc in ("sorted", "atomic"):
+                ms = []
+                for n in range(d):
+                    sch = P.mttkrp_default_schedule(T.handle, n, dt, R)
+                    sch.scatter = P.SCATTERS[sc]
+                    o = out[: w.dims[n]]
+                    ms.append(ev_time(lambda: T.mttkrp(n, facs, R, out=o, sched=sch), 3))
+                t = sum(ms) / d / 1e3
+                row = {"R": R, "factors": dt, "scatter": sc, "ms_per_mode": ms,
+                       "nnzR_per_s": w.nnz * R * d / (sum(ms) / 1e3),
+                       "paper_model_GBps": ((d * R + 3) * s_r + d * s_o) * w.nnz / t / 1e9}
+                row["paper_model_frac_of_peak"] = row["paper_model_GBps"] / peak_gbs
+                if dt == "f64":
+                    row["fp64_frac_of_fma_peak"] = w.nnz * R * d / t / fma["f64"]
+                rows.append(row)
+            del facs, out
+    # 10 CP-ALS iterations at R = 128 on the coalesced tensor (captured graph)
+    Tc = P.SparseTensor(idx, vals, w.dims, coalesce=True)
+    Tc.build_permutation()
+    cp = {}
+    R = 128
+    ld = P.factor_ld(R)
+    for dt in ("f32", "bf16"):
+        fnp = synth.factor_matrices(w.dims, R, 11, "uniform", dtype=dt)
+        facs = [_dev_factor(torch, f, dt) for f in fnp]
+        lam = torch.zeros(R, dtype=torch.float64, device="cuda")
+        fit = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ws = Tc.cp_als_workspace(R, ld)
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            Tc.cp_als_step(facs, R, lam, fit, ws)  # capture
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(side)
+            for _ in range(10):
+                Tc.cp_als_step(facs, R, lam, fit, ws)
+            e1.record(side)
+        torch.cuda.synchronize()
+        P.cp_als_status(ws.data_ptr(), side.cuda_stream)
+        cp[dt] = {"s_per_10_iterations": e0.elapsed_time(e1) / 1e3, "fit": float(fit.item())}
+    # the FP64 oracle's MTTKRP on one host core, sampled and scaled to the tensor
+    sample = min(w.nnz, 1_000_000)
+    A64 = [np.random.default_rng(m).random((I, R)) for m, I in enumerate(w.dims)]
+    t0 = time.perf_counter()
+    for n in range(d):
+        oracle.mttkrp(idx[:, :sample], vals[:sample], w.dims, A64, n, R)
+    t_or = (time.perf_counter() - t0) * w.nnz / sample
+    best = {}
+    for r in rows:
+        k = (r["factors"], r["scatter"])
+        best[k] = max(best.get(k, 0.0), r["paper_model_frac_of_peak"])
+    line = {"metric": "paper sweep: MTTKRP nnz*R/s and bandwidth model vs R; CP-ALS 10 iterations",
+            "workload": w.name, "dims": w.dims, "nnz": w.nnz, "nnz_coalesced": Tc.nnz,
+            "hbm_peak_GBps": peak_gbs, "peak_kind": peak_kind,
+            "fma_probe_flops": fma, "sweep": rows, "cp_als_R128": cp,
+            "oracle_mttkrp_s_per_iteration_1core": t_or,
+            "speedup_vs_1core_oracle_mttkrp": {dt: 10 * t_or / v["s_per_10_iterations"] for dt, v in cp.items()},
+            "best_paper_model_frac": {f"{k[0]}/{k[1]}": v for k, v in best.items()}}
+    print(json.dumps(line), flush=True)
+    Tc.close()
+    T.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.paper_sweep:
+        run_paper_sweep(a)
     elif a.cpals:
         run_cpals(a)
     elif a.batched:

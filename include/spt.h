@@ -3,9 +3,9 @@
  *
  * Method: Phipps & Kolda, "Software for Sparse Tensor Decomposition on
  * Emerging Computing Architectures" (arXiv 1809.09175).  The tensor is a COO
- * list of P nonzeros x_i with coordinates (l_i1..l_id) (Sec. 2); the kernel
- * is the mode-n MTTKRP of Sec. 2 eq. (mttkrp); the permuted traversal is
- * Sec. 5 (Fig. "MTTKRP-C"); CP-ALS is the alternating least squares of Sec. 2.
+ * list of P nonzeros x_i with coordinates (l_i1..l_id) (Sec. 3); the kernel
+ * is the mode-n MTTKRP of Sec. 3 eq. (mttkrp); the permuted traversal is
+ * Sec. 6 (Fig. "MTTKRP-C"); CP-ALS is the alternating least squares of Sec. 3.
  *
  * Conventions for every call
  *  - Nothing throws across the ABI.  Every call returns an spt_status; on
@@ -46,7 +46,10 @@ typedef enum {
     SPT_ESTATE = 8        /* the call needs an earlier step (e.g. a coalesced tensor) */
 } spt_status;
 
-typedef enum { SPT_F32 = 0, SPT_BF16 = 1, SPT_F16 = 2 } spt_dtype;
+/* Factor storage types.  SPT_F64 (fp64 factors, fp64 accumulation and
+ * output: the precision of the paper's measurements, Sec. 7) is supported by
+ * mttkrp and the schedule tools, not by cp_als_step or the batch. */
+typedef enum { SPT_F32 = 0, SPT_BF16 = 1, SPT_F16 = 2, SPT_F64 = 3 } spt_dtype;
 
 /* tensor_create_coo flags */
 #define SPT_DEVICE_PTRS 1 /* idx / vals are device pointers (copied, not adopted) */
@@ -55,12 +58,18 @@ typedef enum { SPT_F32 = 0, SPT_BF16 = 1, SPT_F16 = 2 } spt_dtype;
 /* build_mode_permutation flags */
 #define SPT_PERM_INDEX_ONLY 1 /* keep only the permutation, not the mode-sorted copy */
 
-/* Scatter strategies of the MTTKRP (Sec. 3-5). */
+/* Scatter strategies of the MTTKRP (Sec. 4-6). */
 typedef enum {
     SPT_SCATTER_AUTO = 0,   /* library choice (learned selector if loaded, else rule) */
     SPT_SCATTER_ATOMIC = 1, /* storage order, every row flush is an atomic add (Fig. MTTKRP-B) */
     SPT_SCATTER_PERM = 2,   /* permuted traversal through the mode-n permutation (Fig. MTTKRP-C) */
-    SPT_SCATTER_SORTED = 3  /* permuted traversal over a mode-n-sorted copy of the nonzeros */
+    SPT_SCATTER_SORTED = 3, /* permuted traversal over a mode-n-sorted copy of the nonzeros */
+    SPT_SCATTER_PRIVATE = 4 /* storage order, row flushes added into a private copy of the
+                             * output in shared memory (split over a cluster of up to 8
+                             * CTAs when one CTA's cannot hold it), added to `out` at the
+                             * end: the privatised scatter Sec. 8 proposes for short
+                             * modes.  Needs no permutation; SPT_EINVAL when I_n rows
+                             * of R floats do not fit 8 CTAs' shared memory. */
 } spt_scatter;
 
 /* A launch schedule of the MTTKRP kernel.
@@ -88,9 +97,9 @@ typedef struct {
 /* Message of the last failed call on this host thread ("" if none). */
 const char *spt_last_error(void);
 
-/* ---- tensor ingest (Sec. 2, COO; Sec. 3.2 storage) --------------------- */
+/* ---- tensor ingest (Sec. 3, COO; Sec. 4.2 storage) --------------------- */
 
-/* Create a COO tensor (Sec. 2: a P-vector of values and P x d coordinates).
+/* Create a COO tensor (Sec. 3: a P-vector of values and P x d coordinates).
  *  order     : d in [1, 8].
  *  dims      : host, d mode lengths I_m in [1, 2^31 - 1].
  *  nnz       : P in [0, 2^31 - 1].
@@ -103,7 +112,7 @@ const char *spt_last_error(void);
  * keeps ownership of its buffers.  Coordinates are range-checked on the
  * device; this call synchronises `stream` to read the check and returns
  * SPT_ERANGE (creating nothing) if a coordinate is outside [0, I_m).
- * SPT_COALESCE sums duplicates (Sec. 2: an entry is the sum of the nonzeros
+ * SPT_COALESCE sums duplicates (Sec. 3: an entry is the sum of the nonzeros
  * stored at its coordinate), leaving distinct coordinates in lexicographic
  * order; it is required by cp_als_step, whose fit needs ||X||. */
 spt_status tensor_create_coo(int order, const int64_t *dims, int64_t nnz,
@@ -128,9 +137,9 @@ spt_status tensor_norm2(spt_tensor t, double *out);
  * SPT_ETIMEOUT if a kernel's bounded wait ran out since the tensor was made. */
 spt_status tensor_check(spt_tensor t, void *stream);
 
-/* ---- mode permutations (Sec. 5) --------------------------------------- */
+/* ---- mode permutations (Sec. 6) --------------------------------------- */
 
-/* Build the mode-n permutation of Sec. 5: perm_n lists nonzero positions in
+/* Build the mode-n permutation of Sec. 6: perm_n lists nonzero positions in
  * increasing mode-n coordinate, ties in storage order (a stable sort, done
  * by an on-device LSD radix sort).  mode = -1 builds all modes.  Unless
  * flags has SPT_PERM_INDEX_ONLY, the nonzeros are also copied in perm_n
@@ -171,7 +180,7 @@ spt_status tensor_get_permutation(spt_tensor t, int mode, int32_t *perm, void *s
 spt_status mode_permutation_noalloc(const int32_t *keys, int64_t n, int64_t dim, int32_t *perm,
                                     void *stream);
 
-/* ---- MTTKRP (Sec. 2 eq. mttkrp; Figs. MTTKRP-A/B/C) -------------------- */
+/* ---- MTTKRP (Sec. 3 eq. mttkrp; Figs. MTTKRP-A/B/C) -------------------- */
 
 /* Mode-n MTTKRP:  out(k, j) = lambda_j * sum_{i : l_in = k} x_i *
  *                             prod_{m != n} A^(m)(l_im, j)
@@ -180,14 +189,17 @@ spt_status mode_permutation_noalloc(const int32_t *keys, int64_t n, int64_t dim,
  *            I_m x ld of type fdt.  factors[mode] is not read (may be NULL).
  *  rank    : R >= 1.  ld : row stride of the factors and of out (elements,
  *            multiple of 8, >= rank).
- *  lambda  : device, rank float32 weights, or NULL for all ones.
- *  out     : device float32 I_n x ld; overwritten (columns >= rank set to 0).
+ *  lambda  : device, rank weights (float32; float64 when fdt is SPT_F64), or
+ *            NULL for all ones.
+ *  out     : device I_n x ld, float32 (float64 when fdt is SPT_F64), 16-byte
+ *            aligned; overwritten (columns >= rank set to 0).
  *  sched   : NULL = library choice; else the schedule to run (SPT_SCATTER_PERM
  *            and SPT_SCATTER_SORTED need build_mode_permutation(mode)).
- * Accumulation is float32.  The atomic and permuted strategies add in
- * different orders, so results agree to rounding, not bit for bit. */
+ * Accumulation is float32 (float64 for SPT_F64).  The atomic and permuted
+ * strategies add in different orders, so results agree to rounding, not bit
+ * for bit. */
 spt_status mttkrp(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt, int rank,
-                  int ld, const float *lambda, float *out, const spt_schedule *sched,
+                  int ld, const void *lambda, void *out, const spt_schedule *sched,
                   void *stream);
 
 /* Record the schedule to use for (mode, fdt, rank) wherever no schedule is
@@ -200,7 +212,7 @@ spt_status tensor_set_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank, 
 spt_status mttkrp_default_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank,
                                    spt_schedule *out);
 
-/* Tab. "sizes" (Sec. 4): the GPU vector_size and factor block size FBS the
+/* Tab. "sizes" (Sec. 5): the GPU vector_size and factor block size FBS the
  * paper uses for rank R. Host logic. */
 spt_status mttkrp_paper_sizes(int rank, int *vector_size, int *fbs);
 
@@ -211,22 +223,24 @@ spt_status mttkrp_paper_schedule(int rank, spt_dtype fdt, int scatter, spt_sched
 /* ---- schedule search: candidates, autotuner, features, learned selector -- */
 /* Not in the paper, whose schedule is the fixed rule of Tab. "sizes". */
 
-#define SPT_NUM_CANDIDATES 36 /* fixed list of candidate schedules per (tensor, mode, rank) */
+#define SPT_NUM_CANDIDATES 48 /* fixed list of candidate schedules per (tensor, mode, rank) */
 #define SPT_NUM_FEATURES 12   /* per-mode features of tensor_mode_features() */
 
 /* The candidate schedules for rank R (host logic): candidate q combines a
- * scatter strategy (sorted / atomic / perm), a lane layout (ceil(R/4) lanes
+ * scatter strategy (sorted / atomic / perm / private), a lane layout (ceil(R/4) lanes
  * rounded to a power of two with one chunk, or half as many lanes with two
  * chunks), about 96, 192 or 384 nonzeros per warp chunk, and 4 or 8 warps per
  * CTA.  out: SPT_NUM_CANDIDATES schedules; valid (nullable): 1 where the
  * candidate can run on this tensor (its permutation / copy is built, it fits
- * shared memory). */
+ * shared memory, a private copy of the output fits a cluster; judged for
+ * 4-byte accumulators, i.e. any fdt but SPT_F64, which mttkrp_autotune and
+ * mttkrp_select check for themselves). */
 spt_status mttkrp_candidates(spt_tensor t, int mode, int rank, spt_schedule *out, int *valid);
 
 /* Time one schedule: a warm-up launch, then the fastest of `reps` launches
  * (CUDA events).  Arguments as mttkrp(); synchronises `stream`. *ms in ms. */
 spt_status mttkrp_time_schedule(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt,
-                                int rank, int ld, float *out, const spt_schedule *sched, int reps,
+                                int rank, int ld, void *out, const spt_schedule *sched, int reps,
                                 float *ms, void *stream);
 
 /* Exhaustive autotuner: time every valid candidate (mttkrp_time_schedule)
@@ -235,7 +249,7 @@ spt_status mttkrp_time_schedule(spt_tensor t, int mode, const void *const *facto
  * time, -1 for invalid ones: the training data of the learned selector.
  * `out` is scratch output (I_mode x ld float32).  Synchronises `stream`. */
 spt_status mttkrp_autotune(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt, int rank,
-                           int ld, float *out, int reps, spt_schedule *best, float *best_ms,
+                           int ld, void *out, int reps, spt_schedule *best, float *best_ms,
                            float *times, void *stream);
 
 /* Per-mode features (host output, SPT_NUM_FEATURES floats): order, log2 I_n,
@@ -294,7 +308,7 @@ typedef struct spt_batch_s *spt_batch; /* opaque, library-owned */
 
 /* One tensor of a batch.  The MTTKRP definition is that of mttkrp() (unit
  * weights); the traversal is the permuted one over the mode-sorted copy
- * (Sec. 5), so every listed mode needs build_mode_permutation() without
+ * (Sec. 6), so every listed mode needs build_mode_permutation() without
  * SPT_PERM_INDEX_ONLY.
  *  tensor  : order 2..5.   mode : -1 = every mode, else one mode.
  *  rank, ld: as for mttkrp(); factors and outputs share ld.
@@ -336,12 +350,41 @@ spt_status mttkrp_batch_check(spt_batch b, void *stream);
 /* Free a batch (synchronises the device). */
 spt_status mttkrp_batch_destroy(spt_batch b);
 
-/* ---- CP-ALS (Sec. 2) -------------------------------------------------- */
+/* ---- generalised CP gradient (Sec. 8: count and binary data) ---------- */
+
+/* Losses of gcp_gradient, with m the model value sum_j prod_l A^(l)(e_l, j)
+ * of an entry e and x its value. */
+typedef enum {
+    SPT_LOSS_POISSON = 0,         /* f = m - x log m over EVERY entry of the tensor (x = 0 off the
+                                   * stored coordinates; duplicates add); needs m > 0 at the
+                                   * stored entries (e.g. nonnegative factors) */
+    SPT_LOSS_BERNOULLI_LOGIT = 1, /* f = log(1 + e^m) - x m over the STORED entries only (store
+                                   * sampled zeros explicitly; each stored copy is one term) */
+    SPT_LOSS_GAUSSIAN = 2         /* f = (m - x)^2 over the stored entries */
+} spt_loss;
+
+/* Gradient of the generalised CP loss F = sum f(x_e, m_e) with respect to
+ * A^(n):  grad(k, j) = sum_{e : e_n = k} df/dm(x_e, m_e) prod_{l != n} A^(l)(e_l, j)
+ * -- an MTTKRP whose values are df/dm at the model value (computed with
+ * A^(n) itself), run over the mode-sorted copy.  For SPT_LOSS_POISSON the
+ * entries off the stored coordinates (df/dm = 1) contribute
+ * prod_{l != n} colsum_l(j) to every row, added in fp64.
+ *  factors : host array of d device pointers, ALL read (including factors[mode]),
+ *            row-major I_m x ld, fdt in {SPT_F32, SPT_BF16, SPT_F16}.
+ *  rank    : 1..256 (one rank block of the kernel).  ld as for mttkrp.
+ *  grad    : device float32 I_n x ld, 16-byte aligned; overwritten (columns >= rank 0).
+ *  loss_out: device double or NULL; set to F (fp32 terms, fp64 sums).
+ * Needs build_mode_permutation(mode) (SPT_ESTATE otherwise); order 2..5.
+ * Allocates a d x rank fp64 scratch (stream-ordered) for the Poisson loss. */
+spt_status gcp_gradient(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt, int rank, int ld,
+                        int loss, float *grad, double *loss_out, void *stream);
+
+/* ---- CP-ALS (Sec. 3) -------------------------------------------------- */
 
 /* Workspace bytes cp_als_step needs for this tensor, rank and ld. */
 spt_status cp_als_workspace_size(spt_tensor t, int rank, int ld, size_t *bytes);
 
-/* One CP-ALS iteration over all modes n = 0..d-1 in order (Sec. 2, ALS):
+/* One CP-ALS iteration over all modes n = 0..d-1 in order (Sec. 3, ALS):
  *   V = MTTKRP_n(X, A) (unit weights); H = elementwise product over m != n of
  *   A^(m)T A^(m) (FP64); Cholesky H = L L^T (FP64, one retry with a ridge of
  *   1e-12 trace(H)/R); A^(n) = V H^-1; lambda_j = ||A^(n)(:,j)||_2 (FP64) and
@@ -368,9 +411,17 @@ spt_status cp_als_status(void *workspace, void *stream);
 
 /* STREAM-style copy dst[0:bytes) = src[0:bytes) with this library's own
  * kernel (16-byte vector loads/stores, persistent grid); the bandwidth
- * denominator of Sec. 6 ("peak bandwidth via STREAM"). bytes % 16 == 0,
+ * denominator that Sec. 7 takes from STREAM. bytes % 16 == 0,
  * both pointers 16-byte aligned. */
 spt_status spt_stream_copy(const void *src, void *dst, size_t bytes, void *stream);
+
+/* FMA-rate probe (no counterpart in the paper): enqueue a kernel in which
+ * every thread of a grid of 8 CTAs of 256 threads per SM runs 8 independent
+ * FMA chains of `iters` steps in dt (SPT_F32 or SPT_F64).  *flops (host)
+ * receives the floating-point operations it performs (2 per FMA); time the
+ * launch with events on `stream` to get the device's FMA throughput.  sink is
+ * a device double that the kernel never writes in practice. */
+spt_status spt_fma_probe(spt_dtype dt, int64_t iters, double *sink, double *flops, void *stream);
 
 /* Convert n float32 values to fdt storage (round to nearest even). */
 spt_status spt_convert_f32(const float *src, void *dst, spt_dtype fdt, int64_t n, void *stream);

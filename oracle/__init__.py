@@ -44,6 +44,9 @@ def lib():
         L.oracle_cp_als_iter.argtypes = [C.c_int, _lp, C.c_int64, _ip, _dp, C.c_int,
                                          C.POINTER(_dp), _dp, C.c_int, C.c_double, _dp]
         L.oracle_cp_als_iter.restype = C.c_int
+        L.oracle_gcp_grad.argtypes = [C.c_int, _lp, C.c_int64, _ip, _dp, C.c_int, C.c_int,
+                                      C.POINTER(_dp), _lp, C.c_int, _dp, C.c_int64]
+        L.oracle_gcp_grad.restype = C.c_double
         L.oracle_mlp_forward.argtypes = [C.c_int] * 5 + [_dp] * 10
         L.oracle_mlp_loss_grad.argtypes = [C.c_int] * 5 + [_dp] * 15
         L.oracle_mlp_loss_grad.restype = C.c_double
@@ -88,7 +91,7 @@ def _fac_ptrs(factors: Sequence[np.ndarray]):
 
 
 def mttkrp(idx, vals, dims, factors, n: int, R: int, lam=None, ld: Optional[int] = None):
-    """Mode-``n`` MTTKRP by the definition (Sec. 2 eq. mttkrp); returns I_n x ld."""
+    """Mode-``n`` MTTKRP by the definition (Sec. 3 eq. mttkrp); returns I_n x ld."""
     idx, vals = _prep(idx, vals)
     d, P = idx.shape
     dims_a = np.array(dims, dtype=np.int64)
@@ -116,8 +119,26 @@ def mttkrp_rows(idx, vals, dims, factors, n: int, R: int, rows, lam=None):
     return V
 
 
+GCP_LOSSES = {"poisson": 0, "bernoulli": 1, "gaussian": 2}
+
+
+def gcp_grad(idx, vals, dims, factors, n: int, R: int, loss: str, ld: Optional[int] = None):
+    """Generalised CP loss F and its gradient with respect to A^(n) (I_n x ld),
+    by the definition in ``oracle.c`` (Poisson over every entry of the
+    tensor, Bernoulli-logit and Gaussian over the stored entries)."""
+    idx, vals = _prep(idx, vals)
+    d, P = idx.shape
+    dims_a = np.array(dims, dtype=np.int64)
+    fs, arr, lda = _fac_ptrs(factors)
+    ld = R if ld is None else ld
+    G = np.zeros((int(dims[n]), ld), dtype=np.float64)
+    F = lib().oracle_gcp_grad(d, _l(dims_a), P, _i(idx), _d(vals), n, R, arr, _l(lda),
+                              GCP_LOSSES[loss], _d(G), ld)
+    return G, F
+
+
 def stable_argsort(keys) -> np.ndarray:
-    """Positions ordered by (key, position) -- the mode permutation of Sec. 5."""
+    """Positions ordered by (key, position) -- the mode permutation of Sec. 6."""
     keys = np.ascontiguousarray(keys, dtype=np.int32)
     perm = np.empty(keys.shape[0], dtype=np.int32)
     lib().oracle_stable_argsort(keys.shape[0], _i(keys), _i(perm))

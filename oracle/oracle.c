@@ -14,9 +14,9 @@
  *
  * Layout conventions (shared with the tests, not with the CUDA code):
  *   idx   : d*P int32, mode-major; idx[m*P + i] is the 0-based mode-m
- *           coordinate of nonzero i (the paper's l_{i,m+1}, Sec. 2).
+ *           coordinate of nonzero i (the paper's l_{i,m+1}, Sec. 3).
  *   vals  : P doubles (x_i).
- *   A[m]  : I_m x lda[m] row-major factor matrix A^(m) (Sec. 2, eq. CP).
+ *   A[m]  : I_m x lda[m] row-major factor matrix A^(m) (Sec. 3, eq. CP).
  *   V     : I_n x ldv row-major.
  */
 #include <math.h>
@@ -26,7 +26,7 @@
 #include <fenv.h>
 
 /* ---------------------------------------------------------------------- */
-/* MTTKRP, Sec. 2 eq. (mttkrp):                                            */
+/* MTTKRP, Sec. 3 eq. (mttkrp):                                            */
 /*   v(k,j) = lambda_j * sum_{i : l_in = k} x_i * prod_{m != n} a^(m)(l_im, j) */
 /* lambda == NULL means lambda_j = 1.  Columns j >= R of V are set to 0.    */
 /* ---------------------------------------------------------------------- */
@@ -90,7 +90,7 @@ void oracle_mttkrp_rows(int d, const int64_t *dims, int64_t P, const int32_t *id
 }
 
 /* ---------------------------------------------------------------------- */
-/* Mode permutation, Sec. 5: perm lists the nonzeros in increasing mode-n   */
+/* Mode permutation, Sec. 6: perm lists the nonzeros in increasing mode-n   */
 /* index; the sort is stable, so equal indices keep their storage order.    */
 /* Definition used here: sort positions by the pair (key, position).        */
 /* ---------------------------------------------------------------------- */
@@ -110,7 +110,7 @@ void oracle_stable_argsort(int64_t P, const int32_t *keys, int32_t *perm)
 }
 
 /* ---------------------------------------------------------------------- */
-/* Coalescing duplicate coordinates (COO, Sec. 2): the tensor entry at a    */
+/* Coalescing duplicate coordinates (COO, Sec. 3): the tensor entry at a    */
 /* coordinate is the sum of all nonzeros stored with that coordinate.       */
 /* Output: distinct coordinates in lexicographic order (mode 0 slowest),    */
 /* each value the FP64 sum of its duplicates in storage order.              */
@@ -167,7 +167,7 @@ double oracle_norm2(int d, int64_t P, const int32_t *idx, const double *vals)
 }
 
 /* ---------------------------------------------------------------------- */
-/* Dense pieces of one CP-ALS update (Sec. 2 refers to ALS; the steps are   */
+/* Dense pieces of one CP-ALS update (Sec. 3 refers to ALS; the steps are   */
 /* the standard normal-equation update).                                    */
 /* ---------------------------------------------------------------------- */
 
@@ -305,6 +305,88 @@ int oracle_cp_als_iter(int d, const int64_t *dims, int64_t P, const int32_t *idx
     }
     free(lda); free(G); free(H); free(L); free(y);
     return status;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Generalised CP gradient (the count- and binary-data losses that Sec. 8   */
+/* names as the next use of the MTTKRP machinery).  Model value of entry i: */
+/*   m_i = sum_j prod_l a^(l)(i_l, j)                                        */
+/* Loss F = sum over the loss's entry set of f(x, m); the gradient of F     */
+/* with respect to A^(n) is                                                  */
+/*   g(k, j) = sum_{entries e of the set, e_n = k} df/dm(x_e, m_e)           */
+/*                                      * prod_{l != n} a^(l)(e_l, j).       */
+/* loss 0, Poisson with identity link: f = m - x log m over EVERY entry of   */
+/*   the tensor (x = 0 off the stored coordinates, a stored coordinate's x   */
+/*   is the sum of its duplicates).  Off the stored coordinates df/dm = 1,   */
+/*   and summing prod_{l != n} a^(l)(e_l, j) over all entries with e_n = k  */
+/*   factorises into prod_{l != n} (sum_r a^(l)(r, j)); so                   */
+/*     g(k, j) = prod_{l != n} colsum_l(j) - sum_{stored i, i_n = k}         */
+/*               (x_i / m_i) prod_{l != n} a^(l)(i_l, j)                     */
+/*     F = sum_j prod_l colsum_l(j) - sum_{stored i} x_i log m_i.            */
+/* loss 1, Bernoulli with logit link: f = log(1 + e^m) - x m over the        */
+/*   STORED entries (sampled zeros are stored explicitly by the caller; a    */
+/*   duplicated coordinate counts once per copy).  df/dm = 1/(1+e^-m) - x.   */
+/* loss 2, Gaussian: f = (m - x)^2 over the stored entries; df/dm = 2(m-x).  */
+/* G: I_n x ldg (columns >= R set to 0).  Returns F.                          */
+/* ---------------------------------------------------------------------- */
+static double model_value(int d, int64_t P, const int32_t *idx, int64_t i, int R,
+                          const double *const *A, const int64_t *lda)
+{
+    double m = 0.0;
+    for (int j = 0; j < R; ++j) {
+        double t = 1.0;
+        for (int l = 0; l < d; ++l) t *= A[l][(int64_t)idx[(int64_t)l * P + i] * lda[l] + j];
+        m += t;
+    }
+    return m;
+}
+
+double oracle_gcp_grad(int d, const int64_t *dims, int64_t P, const int32_t *idx,
+                       const double *vals, int n, int R, const double *const *A,
+                       const int64_t *lda, int loss, double *G, int64_t ldg)
+{
+    int64_t In = dims[n];
+    memset(G, 0, sizeof(double) * (size_t)In * (size_t)ldg);
+    double F = 0.0;
+    for (int64_t i = 0; i < P; ++i) {
+        double x = vals[i];
+        double m = model_value(d, P, idx, i, R, A, lda);
+        double y;
+        if (loss == 0) {
+            y = -x / m;                 /* the stored entry's part of 1 - x/m */
+            F -= x * log(m);
+        } else if (loss == 1) {
+            y = 1.0 / (1.0 + exp(-m)) - x;
+            F += (m > 0.0 ? m + log1p(exp(-m)) : log1p(exp(m))) - x * m;
+        } else {
+            y = 2.0 * (m - x);
+            F += (m - x) * (m - x);
+        }
+        int64_t k = idx[(int64_t)n * P + i];
+        for (int j = 0; j < R; ++j) {
+            double t = y;
+            for (int l = 0; l < d; ++l) {
+                if (l == n) continue;
+                t *= A[l][(int64_t)idx[(int64_t)l * P + i] * lda[l] + j];
+            }
+            G[k * ldg + j] += t;
+        }
+    }
+    if (loss == 0) {
+        /* the df/dm = 1 share of every entry of the tensor */
+        for (int j = 0; j < R; ++j) {
+            double c = 1.0, call = 1.0;
+            for (int l = 0; l < d; ++l) {
+                double cs = 0.0;
+                for (int64_t r = 0; r < dims[l]; ++r) cs += A[l][r * lda[l] + j];
+                call *= cs;
+                if (l != n) c *= cs;
+            }
+            F += call;
+            for (int64_t k = 0; k < In; ++k) G[k * ldg + j] += c;
+        }
+    }
+    return F;
 }
 
 /* ---------------------------------------------------------------------- */

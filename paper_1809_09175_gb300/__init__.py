@@ -1,8 +1,8 @@
 """GB300 (sm_103a) sparse COO MTTKRP and CP-ALS.
 
 Method: Phipps & Kolda, arXiv 1809.09175 -- the mode-n MTTKRP of a COO sparse
-tensor (Sec. 2 eq. mttkrp), its atomic and permuted-traversal scatters
-(Secs. 3-5) and the CP-ALS iteration around it (Sec. 2).  The compute runs
+tensor (Sec. 3 eq. mttkrp), its atomic and permuted-traversal scatters
+(Secs. 4-6) and the CP-ALS iteration around it (Sec. 3).  The compute runs
 in ``libspt.so`` (hand-written CUDA for sm_103a behind the C ABI of
 ``include/spt.h``); :mod:`.binding` marshals arguments to it and
 :mod:`.tensor` adds a thin torch-tensor convenience layer.

@@ -17,16 +17,16 @@ LIB_PATH = os.path.join(HERE, "libspt.so")
 
 SPT_OK, SPT_EINVAL, SPT_ERANGE, SPT_ENOMEM, SPT_ECUDA = 0, 1, 2, 3, 4
 SPT_EUNSUPPORTED, SPT_ESINGULAR, SPT_ETIMEOUT, SPT_ESTATE = 5, 6, 7, 8
-SPT_F32, SPT_BF16, SPT_F16 = 0, 1, 2
+SPT_F32, SPT_BF16, SPT_F16, SPT_F64 = 0, 1, 2, 3
 SPT_DEVICE_PTRS, SPT_COALESCE = 1, 2
 SPT_PERM_INDEX_ONLY = 1
-SPT_SCATTER_AUTO, SPT_SCATTER_ATOMIC, SPT_SCATTER_PERM, SPT_SCATTER_SORTED = 0, 1, 2, 3
+SPT_SCATTER_AUTO, SPT_SCATTER_ATOMIC, SPT_SCATTER_PERM, SPT_SCATTER_SORTED, SPT_SCATTER_PRIVATE = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "SPT_OK", 1: "SPT_EINVAL", 2: "SPT_ERANGE", 3: "SPT_ENOMEM", 4: "SPT_ECUDA",
                 5: "SPT_EUNSUPPORTED", 6: "SPT_ESINGULAR", 7: "SPT_ETIMEOUT", 8: "SPT_ESTATE"}
-DTYPES = {"f32": SPT_F32, "bf16": SPT_BF16, "f16": SPT_F16}
+DTYPES = {"f32": SPT_F32, "bf16": SPT_BF16, "f16": SPT_F16, "f64": SPT_F64}
 SCATTERS = {"auto": SPT_SCATTER_AUTO, "atomic": SPT_SCATTER_ATOMIC, "perm": SPT_SCATTER_PERM,
-            "sorted": SPT_SCATTER_SORTED}
+            "sorted": SPT_SCATTER_SORTED, "private": SPT_SCATTER_PRIVATE}
 
 
 class SptError(RuntimeError):
@@ -99,12 +99,13 @@ _sig("mttkrp_paper_sizes", C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int))
 _sig("mttkrp_paper_schedule", C.c_int, C.c_int, C.c_int, C.POINTER(spt_schedule))
 _sig("spt_stream_copy", _vp, _vp, C.c_size_t, _vp)
 _sig("spt_convert_f32", _vp, _vp, C.c_int, C.c_int64, _vp)
+_sig("spt_fma_probe", C.c_int, C.c_int64, _vp, C.POINTER(C.c_double), _vp)
 
 EXPORTED = ["spt_last_error", "spt_device_info", "tensor_create_coo", "tensor_destroy",
             "tensor_info", "tensor_get_coo", "tensor_norm2", "tensor_check",
             "build_mode_permutation", "tensor_get_permutation", "mttkrp",
             "mttkrp_default_schedule", "tensor_set_schedule", "mttkrp_paper_sizes", "mttkrp_paper_schedule",
-            "spt_stream_copy", "spt_convert_f32"]
+            "spt_stream_copy", "spt_convert_f32", "spt_fma_probe"]
 
 
 def _try_sig(name, *args):
@@ -119,7 +120,10 @@ _try_sig("cp_als_step", _vp, C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _vp, _vp
          C.c_size_t, _vp)
 _try_sig("cp_als_status", _vp, _vp)
 _try_sig("mode_permutation_noalloc", _vp, C.c_int64, C.c_int64, _vp, _vp)
-SPT_NUM_CANDIDATES, SPT_NUM_FEATURES = 36, 12
+_try_sig("gcp_gradient", _vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp)
+SPT_LOSS_POISSON, SPT_LOSS_BERNOULLI_LOGIT, SPT_LOSS_GAUSSIAN = 0, 1, 2
+LOSSES = {"poisson": SPT_LOSS_POISSON, "bernoulli": SPT_LOSS_BERNOULLI_LOGIT, "gaussian": SPT_LOSS_GAUSSIAN}
+SPT_NUM_CANDIDATES, SPT_NUM_FEATURES = 48, 12
 _fp = C.POINTER(C.c_float)
 _try_sig("mttkrp_candidates", _vp, C.c_int, C.c_int, C.POINTER(spt_schedule), C.POINTER(C.c_int))
 _try_sig("mttkrp_time_schedule", _vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _vp,
@@ -257,6 +261,13 @@ def spt_convert_f32(src_ptr: int, dst_ptr: int, fdt, n: int, stream: int = 0):
     _chk(_L.spt_convert_f32(src_ptr, dst_ptr, _dt(fdt), n, stream or None))
 
 
+def spt_fma_probe(fdt, iters: int, sink_ptr: int, stream: int = 0) -> float:
+    """Enqueue the FMA-rate probe; returns the flops it performs."""
+    v = C.c_double()
+    _chk(_L.spt_fma_probe(_dt(fdt), iters, sink_ptr, C.byref(v), stream or None))
+    return v.value
+
+
 def cp_als_workspace_size(t: int, rank: int, ld: int) -> int:
     v = C.c_size_t()
     _chk(_L.cp_als_workspace_size(t, rank, ld, C.byref(v)))
@@ -277,6 +288,14 @@ def mode_permutation_noalloc(keys_ptr: int, n: int, dim: int, perm_ptr: int, str
     """Mode permutation computed in the library's static scratch area, for
     callers that cannot allocate device memory (see include/spt.h)."""
     _chk(_L.mode_permutation_noalloc(keys_ptr or None, n, dim, perm_ptr or None, stream or None))
+
+
+def gcp_gradient(t: int, mode: int, factor_ptrs, fdt, rank: int, ld: int, loss, grad_ptr: int,
+                 loss_ptr: int = 0, stream: int = 0):
+    arr = (_vp * len(factor_ptrs))(*factor_ptrs)
+    lo = LOSSES[loss] if isinstance(loss, str) else int(loss)
+    _chk(_L.gcp_gradient(t, mode, arr, _dt(fdt), rank, ld, lo, grad_ptr, loss_ptr or None,
+                         stream or None))
 
 
 def mttkrp_batch_create(items, fdt):

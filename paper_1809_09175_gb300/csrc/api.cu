@@ -1,5 +1,5 @@
-// api.cu -- C-ABI entry points: errors, tensor ingest (Sec. 2 COO), mode
-// permutations (Sec. 5), the MTTKRP call (Sec. 2 eq. mttkrp) and utilities.
+// api.cu -- C-ABI entry points: errors, tensor ingest (Sec. 3 COO), mode
+// permutations (Sec. 6), the MTTKRP call (Sec. 3 eq. mttkrp) and utilities.
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -238,16 +238,19 @@ spt_status tensor_check(spt_tensor t, void *stream) {
 }
 
 spt_status mttkrp(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt, int rank,
-                  int ld, const float *lambda, float *out, const spt_schedule *sched,
+                  int ld, const void *lambda, void *out, const spt_schedule *sched,
                   void *stream) {
     if (!t) return fail(SPT_EINVAL, "mttkrp: NULL tensor");
     if (mode < 0 || mode >= t->d) return fail(SPT_EINVAL, "mttkrp: mode out of range");
     if (t->d > SPT_MAX_KERNEL_ORDER) return fail(SPT_EUNSUPPORTED, "mttkrp: order > 5");
-    if (fdt != SPT_F32 && fdt != SPT_BF16 && fdt != SPT_F16) return fail(SPT_EINVAL, "mttkrp: bad dtype");
+    if (fdt != SPT_F32 && fdt != SPT_BF16 && fdt != SPT_F16 && fdt != SPT_F64)
+        return fail(SPT_EINVAL, "mttkrp: bad dtype");
     if (rank < 1) return fail(SPT_EINVAL, "mttkrp: rank must be >= 1");
     if (ld < rank || ld % 8) return fail(SPT_EINVAL, "mttkrp: ld must be >= rank and a multiple of 8");
     if (ld > (1 << 28)) return fail(SPT_EUNSUPPORTED, "mttkrp: ld above 2^28 elements");
     if (!out || ((uintptr_t)out & 15)) return fail(SPT_EINVAL, "mttkrp: out NULL or not 16-byte aligned");
+    if (lambda && ((uintptr_t)lambda & (acc_bytes(fdt) - 1)))
+        return fail(SPT_EINVAL, "mttkrp: lambda not aligned to its element");
     if (t->d > 1 && !factors) return fail(SPT_EINVAL, "mttkrp: factors is NULL");
     for (int m = 0; m < t->d; ++m) {
         if (m == mode) continue;
@@ -283,7 +286,7 @@ spt_status mttkrp_default_schedule(spt_tensor t, int mode, spt_dtype fdt, int ra
     return SPT_OK;
 }
 
-// Tab. "sizes" (Sec. 4): GPU vector_size and factor block size FBS by rank.
+// Tab. "sizes" (Sec. 5): GPU vector_size and factor block size FBS by rank.
 spt_status mttkrp_paper_sizes(int R, int *vector_size, int *fbs) {
     if (R < 1) return fail(SPT_EINVAL, "mttkrp_paper_sizes: rank must be >= 1");
     int vs, fb;

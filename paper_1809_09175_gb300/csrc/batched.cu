@@ -6,7 +6,7 @@
 // claims items with an atomic counter (uneven tensors balance themselves),
 // stages each item's records with a bulk copy while the previous item is
 // computed, and runs the same per-chunk routine as the single-tensor kernel
-// (Sec. 5 permuted traversal over sorted nonzeros, Fig. MTTKRP-C).  One
+// (Sec. 6 permuted traversal over sorted nonzeros, Fig. MTTKRP-C).  One
 // zero-fill kernel clears every output and the counter first; the two
 // launches are captured once in a CUDA graph and replayed.
 #include <vector>
@@ -53,7 +53,7 @@ template <typename FT, int C, int D1>
 __device__ __forceinline__ void run_chunk(const MttkrpParams &p, const int32_t *buf, int n) {
     int b0, b1;
     chunk_bounds<D1, M_SORTED>(p, buf, n, b0, b1);
-    mttkrp_chunk<FT, C, D1, M_SORTED>(p, buf, n, b0, b1, nullptr);
+    mttkrp_chunk<FT, C, D1, M_SORTED>(p, buf, n, b0, b1, nullptr, nullptr);
 }
 
 template <typename FT>
@@ -209,6 +209,7 @@ spt_status mttkrp_batch_create(int count, const spt_batch_item *items, spt_dtype
     if (!out || (count > 0 && !items)) return fail(SPT_EINVAL, "mttkrp_batch_create: NULL argument");
     *out = nullptr;
     if (count < 0) return fail(SPT_EINVAL, "mttkrp_batch_create: negative count");
+    if (fdt == SPT_F64) return fail(SPT_EUNSUPPORTED, "mttkrp_batch_create: fp64 factors are supported by mttkrp only");
     if (fdt != SPT_F32 && fdt != SPT_BF16 && fdt != SPT_F16) return fail(SPT_EINVAL, "mttkrp_batch_create: bad dtype");
     spt_batch b = new (std::nothrow) spt_batch_s();
     if (!b) return fail(SPT_ENOMEM, "mttkrp_batch_create: host allocation");

@@ -117,6 +117,44 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// ---- thread-block clusters (distributed shared memory) ----
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Barrier over every thread of every CTA of the cluster; release/acquire
+// orders the shared-memory writes before it against the reads after it.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+
+// Shared-memory address `addr` of this CTA mapped to the same offset in the
+// shared memory of cluster CTA `rank`.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// Atomic add into this CTA's shared memory.
+__device__ __forceinline__ void red_add_shared(uint32_t addr, float v) {
+    asm volatile("red.shared::cta.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_shared(uint32_t addr, double v) {
+    asm volatile("red.shared::cta.add.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+
+// Atomic add into (possibly another CTA's) shared memory of the cluster.
+__device__ __forceinline__ void red_add_cluster(uint32_t addr, float v) {
+    asm volatile("red.relaxed.cluster.shared::cluster.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_cluster(uint32_t addr, double v) {
+    asm volatile("red.relaxed.cluster.shared::cluster.add.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+
 // Bounded wait for phase `parity` of `bar`.  Returns true when the phase
 // completed, false when the try budget ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
@@ -140,11 +178,13 @@ __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w 
 
 // Element traits: every lane works on chunks of VEC = 4 consecutive factor
 // columns, loaded as one vector (16 bytes for fp32, 8 bytes for 16-bit
-// types) and widened to float.
+// types, two 16-byte loads for fp64) and widened to the accumulator type Acc
+// (float, or double for fp64 factors).
 template <typename T> struct Elem;
 template <> struct Elem<float> {
     static constexpr int VEC = 4;
     static constexpr int BYTES = 4;
+    typedef float Acc;
     typedef uint4 Raw;
     __device__ __forceinline__ static Raw load(const void *p) {
         return __ldg(reinterpret_cast<const uint4 *>(p));
@@ -157,6 +197,7 @@ template <> struct Elem<float> {
 template <> struct Elem<__nv_bfloat16> {
     static constexpr int VEC = 4;
     static constexpr int BYTES = 2;
+    typedef float Acc;
     typedef uint2 Raw;
     __device__ __forceinline__ static Raw load(const void *p) {
         return __ldg(reinterpret_cast<const uint2 *>(p));
@@ -168,6 +209,7 @@ template <> struct Elem<__nv_bfloat16> {
 template <> struct Elem<__half> {
     static constexpr int VEC = 4;
     static constexpr int BYTES = 2;
+    typedef float Acc;
     typedef uint2 Raw;
     __device__ __forceinline__ static Raw load(const void *p) {
         return __ldg(reinterpret_cast<const uint2 *>(p));
@@ -181,6 +223,28 @@ template <> struct Elem<__half> {
             o[2 * q] = f.x;
             o[2 * q + 1] = f.y;
         }
+    }
+};
+
+struct Raw64 {
+    uint4 lo, hi;
+};
+template <> struct Elem<double> {
+    static constexpr int VEC = 4;
+    static constexpr int BYTES = 8;
+    typedef double Acc;
+    typedef Raw64 Raw;
+    __device__ __forceinline__ static Raw load(const void *p) {
+        Raw r;
+        r.lo = __ldg(reinterpret_cast<const uint4 *>(p));
+        r.hi = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
+        return r;
+    }
+    __device__ __forceinline__ static void widen(const Raw &r, double *o) {
+        o[0] = __hiloint2double((int)r.lo.y, (int)r.lo.x);
+        o[1] = __hiloint2double((int)r.lo.w, (int)r.lo.z);
+        o[2] = __hiloint2double((int)r.hi.y, (int)r.hi.x);
+        o[3] = __hiloint2double((int)r.hi.w, (int)r.hi.z);
     }
 };
 

@@ -1,5 +1,5 @@
-// cpals.cu -- one CP-ALS iteration on the device (Sec. 2: alternating least
-// squares; the MTTKRP of Sec. 2 eq. mttkrp is its dominant step).
+// cpals.cu -- one CP-ALS iteration on the device (Sec. 3: alternating least
+// squares; the MTTKRP of Sec. 3 eq. mttkrp is its dominant step).
 //
 // Per mode n (in order 0..d-1):
 //   1. V = MTTKRP_n(X, A)                                (mttkrp kernel)
@@ -43,20 +43,43 @@ template <> __device__ __forceinline__ __nv_bfloat16 st_elem<__nv_bfloat16>(floa
 }
 template <> __device__ __forceinline__ __half st_elem<__half>(float v) { return __float2half_rn(v); }
 
+// Four consecutive elements as floats (p 16-byte aligned for float, 8-byte
+// for the 16-bit types).
+template <typename FT> __device__ __forceinline__ float4 ld_quad(const FT *p);
+template <> __device__ __forceinline__ float4 ld_quad<float>(const float *p) {
+    return *reinterpret_cast<const float4 *>(p);
+}
+template <> __device__ __forceinline__ float4 ld_quad<__nv_bfloat16>(const __nv_bfloat16 *p) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+}
+template <> __device__ __forceinline__ float4 ld_quad<__half>(const __half *p) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Rows of one Gram tile per thread between barriers.
+constexpr int GRAM_ROWS_PER_THREAD = 16;
+
 // G += A^T A over all I rows (A row-major, stride ld, first R columns).
 // Thread (ti, tj) of a team owns the 4 x 4 block G[4ti.., 4tj..] in
-// registers; RS teams of RT*RT threads split the rows of each staged 32-row
-// tile.  FP32 partial sums over at most 256 rows are folded into the CTA's
-// FP64 copy of G in shared memory, which each CTA adds to G atomically.
+// registers; the RS teams of a CTA split the rows of each staged tile of
+// TR = 16 RS rows (quad loads, columns >= R zeroed), so every thread does 16
+// rows of FMAs per tile.  FP32 partial sums over at most 256 rows are folded
+// into the CTA's FP64 copy of G in shared memory, which each CTA adds to G
+// atomically.
 template <typename FT>
 __global__ void __launch_bounds__(1024) gram_kernel(const FT *A, int64_t I, int ld, int R, double *G) {
-    constexpr int TR = 32, SP = MAXR + 4;
     extern __shared__ __align__(16) unsigned char gsm[];
-    float (*s)[SP] = reinterpret_cast<float (*)[SP]>(gsm);
-    double *red = reinterpret_cast<double *>(gsm + sizeof(float) * TR * SP);
-    const int RT = (R + 3) / 4, RP = RT * 4;
+    const int RT = (R + 3) / 4, RP = RT * 4, SP = RP + 4;
     const int team_sz = RT * RT;
     const int RS = blockDim.x / team_sz;
+    const int TR = GRAM_ROWS_PER_THREAD * RS;
+    float *s = reinterpret_cast<float *>(gsm);                                  // TR x SP
+    double *red = reinterpret_cast<double *>(gsm + sizeof(float) * TR * SP);   // RP x RP
     const int team = threadIdx.x / team_sz, tid = threadIdx.x % team_sz;
     const int ti = tid / RT, tj = tid % RT;
     const int RR = RP * RP;
@@ -67,7 +90,7 @@ __global__ void __launch_bounds__(1024) gram_kernel(const FT *A, int64_t I, int 
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    // fold the FP32 partials into the CTA's FP64 block (one team: owned entries)
+    // fold the FP32 partials into the CTA's FP64 block (each team: its entries)
     auto fold = [&]() {
         if (team < RS) {
 #pragma unroll
@@ -84,15 +107,25 @@ __global__ void __launch_bounds__(1024) gram_kernel(const FT *A, int64_t I, int 
     int since = 0;
     for (int64_t r0 = (int64_t)blockIdx.x * TR; r0 < I; r0 += (int64_t)gridDim.x * TR) {
         __syncthreads();
-        for (int e = threadIdx.x; e < TR * RP; e += blockDim.x) {
-            const int r = e / RP, c = e % RP;
-            s[r][c] = (r0 + r < I && c < R) ? ld_elem<FT>(A + (r0 + r) * ld + c) : 0.f;
+        for (int e = threadIdx.x; e < TR * RT; e += blockDim.x) {
+            const int r = e / RT, q = e - r * RT;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r0 + r < I) {
+                v = ld_quad<FT>(A + (r0 + r) * ld + 4 * q);
+                const int c = 4 * q;
+                if (c >= R) v.x = 0.f;
+                if (c + 1 >= R) v.y = 0.f;
+                if (c + 2 >= R) v.z = 0.f;
+                if (c + 3 >= R) v.w = 0.f;
+            }
+            *reinterpret_cast<float4 *>(&s[r * SP + 4 * q]) = v;
         }
         __syncthreads();
         if (team < RS) {
-            for (int r = team; r < TR; r += RS) {
-                const float4 a = *reinterpret_cast<const float4 *>(&s[r][4 * ti]);
-                const float4 b = *reinterpret_cast<const float4 *>(&s[r][4 * tj]);
+            const int rmax = (int)(I - r0 < (int64_t)TR ? I - r0 : (int64_t)TR);
+            for (int r = team; r < rmax; r += RS) {
+                const float4 a = *reinterpret_cast<const float4 *>(&s[r * SP + 4 * ti]);
+                const float4 b = *reinterpret_cast<const float4 *>(&s[r * SP + 4 * tj]);
                 const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
@@ -100,7 +133,7 @@ __global__ void __launch_bounds__(1024) gram_kernel(const FT *A, int64_t I, int 
                     for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
             }
         }
-        since += TR;
+        since += GRAM_ROWS_PER_THREAD;
         if (since >= 256) {
             fold();
             since = 0;
@@ -201,16 +234,19 @@ __global__ void __launch_bounds__(512) chol_inv_kernel(double *G, int d, int n, 
 
 // A32 = V Hinv, column sums of squares.  Thread (rq, cq) computes the 4 x 4
 // block rows [4rq, 4rq+4) x columns [4cq, 4cq+4) of a tile of V's rows; Hinv
-// and the tile (transposed) sit in shared memory, so each k costs two
-// 16-byte shared loads for 16 FMAs.
+// and the tile (transposed, row stride TROWS + 4 against bank conflicts) sit
+// in shared memory, so each k costs two 16-byte shared loads for 16 FMAs.
+// The tile is read with 16-byte loads; sums of squares are FP32 over a
+// thread's 4 rows of a tile, then FP64.
 __global__ void __launch_bounds__(256) solve_kernel(const float *V, int64_t I, int ld, int R,
                                                     const float *Hinv, float *A32, double *colsq) {
     extern __shared__ __align__(16) float shs[];
     const int CT = (R + 3) / 4, RP = CT * 4;
     const int RQ = blockDim.x / CT;          // row quads per tile
     const int TROWS = 4 * RQ;
+    const int TS = TROWS + 4;
     float *Hs = shs;                         // R x RP
-    float *Vt = shs + R * RP;                // R x TROWS (transposed tile)
+    float *Vt = shs + R * RP;                // R x TS (transposed tile)
     __shared__ double csq[MAXR + 4];
     for (int e = threadIdx.x; e < R * RP; e += blockDim.x) {
         const int k = e / RP, c = e % RP;
@@ -222,9 +258,14 @@ __global__ void __launch_bounds__(256) solve_kernel(const float *V, int64_t I, i
     double local[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t r0 = (int64_t)blockIdx.x * TROWS; r0 < I; r0 += (int64_t)gridDim.x * TROWS) {
         __syncthreads();
-        for (int e = threadIdx.x; e < TROWS * R; e += blockDim.x) {
-            const int r = e / R, k = e % R;
-            Vt[k * TROWS + r] = (r0 + r < I) ? V[(r0 + r) * ld + k] : 0.f;
+        for (int e = threadIdx.x; e < TROWS * CT; e += blockDim.x) {
+            const int r = e / CT, q = e - r * CT;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r0 + r < I) v = *reinterpret_cast<const float4 *>(V + (r0 + r) * ld + 4 * q);
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (4 * q + c < R) Vt[(4 * q + c) * TS + r] = vv[c];
         }
         __syncthreads();
         if (act) {
@@ -234,7 +275,7 @@ __global__ void __launch_bounds__(256) solve_kernel(const float *V, int64_t I, i
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
             for (int k = 0; k < R; ++k) {
-                const float4 v = *reinterpret_cast<const float4 *>(&Vt[k * TROWS + 4 * rq]);
+                const float4 v = *reinterpret_cast<const float4 *>(&Vt[k * TS + 4 * rq]);
                 const float4 h = *reinterpret_cast<const float4 *>(&Hs[k * RP + 4 * cq]);
                 const float vv[4] = {v.x, v.y, v.z, v.w}, hh[4] = {h.x, h.y, h.z, h.w};
 #pragma unroll
@@ -242,53 +283,104 @@ __global__ void __launch_bounds__(256) solve_kernel(const float *V, int64_t I, i
 #pragma unroll
                     for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(vv[i], hh[j], acc[i][j]);
             }
+            float sq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int64_t row = r0 + 4 * rq + i;
                 if (row >= I) continue;
+                // columns >= R of A32 are never read
+                *reinterpret_cast<float4 *>(A32 + row * ld + 4 * cq) =
+                    make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = 4 * cq + j;
-                    if (c < R) {
-                        A32[row * ld + c] = acc[i][j];
-                        local[j] += (double)acc[i][j] * (double)acc[i][j];
-                    }
-                }
+                for (int j = 0; j < 4; ++j) sq[j] = fmaf(acc[i][j], acc[i][j], sq[j]);
             }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) local[j] += (double)sq[j];
         }
     }
     if (act)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) atomicAdd(&csq[4 * cq + j], local[j]);
+        for (int j = 0; j < 4; ++j)
+            if (4 * cq + j < R) atomicAdd(&csq[4 * cq + j], local[j]);
     __syncthreads();
     for (int e = threadIdx.x; e < R; e += blockDim.x) atomicAdd(colsq + e, csq[e]);
 }
 
-// lambda_j = ||A32(:,j)||, store A32/lambda in the factor's type (padding
-// columns zero); on the last mode accumulate <X,M> = sum V(k,j) lambda_j A(k,j).
+// Store the four elements of a quad in the factor's type (16 or 8 bytes).
+template <typename FT> __device__ __forceinline__ void st_quad(FT *p, const float (&v)[4], float (&back)[4]);
+template <> __device__ __forceinline__ void st_quad<float>(float *p, const float (&v)[4], float (&back)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) back[c] = v[c];
+}
+template <>
+__device__ __forceinline__ void st_quad<__nv_bfloat16>(__nv_bfloat16 *p, const float (&v)[4], float (&back)[4]) {
+    __nv_bfloat16 b[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        b[c] = __float2bfloat16_rn(v[c]);
+        back[c] = __bfloat162float(b[c]);
+    }
+    *reinterpret_cast<uint2 *>(p) = *reinterpret_cast<const uint2 *>(b);
+}
+template <> __device__ __forceinline__ void st_quad<__half>(__half *p, const float (&v)[4], float (&back)[4]) {
+    __half b[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        b[c] = __float2half_rn(v[c]);
+        back[c] = __half2float(b[c]);
+    }
+    *reinterpret_cast<uint2 *>(p) = *reinterpret_cast<const uint2 *>(b);
+}
+
+// lambda_j = ||A32(:,j)||, store A32 * (1/lambda_j) in the factor's type
+// (padding columns zero; a zero column is kept as is); on the last mode
+// accumulate <X,M> = sum V(k,j) lambda_j A(k,j) (FP32 over a quad, then FP64).
+// Thread t handles quad t % (ld/4) of rows t / (ld/4), +rows per pass, ...
 template <typename FT>
-__global__ void normalize_kernel(const float *A32, const float *V, int64_t I, int ld, int R,
-                                 const double *colsq, FT *A, double *lambda, int last,
-                                 double *inner) {
+__global__ void __launch_bounds__(256) normalize_kernel(const float *A32, const float *V, int64_t I, int ld,
+                                                        int R, const double *colsq, FT *A, double *lambda,
+                                                        int last, double *inner) {
+    __shared__ float sinv[MAXR + 8], slam[MAXR + 8];
+    for (int j = threadIdx.x; j < R; j += blockDim.x) {
+        const double l = sqrt(colsq[j]);
+        slam[j] = (float)l;
+        sinv[j] = l > 0.0 ? (float)(1.0 / l) : 1.0f;
+        if (blockIdx.x == 0) lambda[j] = l;
+    }
+    __syncthreads();
+    const int q4 = ld >> 2;
+    const bool wide = q4 > (int)blockDim.x;
+    const int qi = wide ? (int)threadIdx.x : (int)threadIdx.x % q4;
+    const int qstep = wide ? (int)blockDim.x : q4;
+    const int rr = wide ? 0 : (int)threadIdx.x / q4;
+    const int rpp = wide ? 1 : (int)blockDim.x / q4;
     double local = 0.0;
-    const int64_t total = I * ld;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e % ld);
-        float out = 0.f;
-        if (j < R) {
-            const double lam = sqrt(colsq[j]);
-            const float a = A32[e];
-            out = lam > 0.0 ? (float)((double)a / lam) : a;
-            const FT st = st_elem<FT>(out);
-            A[e] = st;
-            if (last) local += (double)V[e] * lam * (double)ld_elem<FT>(&st);
-        } else {
-            A[e] = st_elem<FT>(0.f);
+    if (rr < rpp) {
+        for (int64_t row = (int64_t)blockIdx.x * rpp + rr; row < I; row += (int64_t)gridDim.x * rpp) {
+            for (int q = qi; q < q4; q += qstep) {
+                const int64_t e = row * ld + 4 * q;
+                float o[4] = {0.f, 0.f, 0.f, 0.f}, back[4];
+                if (4 * q < R) {
+                    const float4 a = *reinterpret_cast<const float4 *>(A32 + e);
+                    const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (4 * q + c < R) o[c] = av[c] * sinv[4 * q + c];
+                }
+                st_quad<FT>(A + e, o, back);
+                if (last && 4 * q < R) {
+                    const float4 v = *reinterpret_cast<const float4 *>(V + e);
+                    const float vv[4] = {v.x, v.y, v.z, v.w};
+                    float sum = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (4 * q + c < R) sum = fmaf(vv[c] * slam[4 * q + c], back[c], sum);
+                    local += (double)sum;
+                }
+            }
         }
     }
-    if (blockIdx.x == 0)
-        for (int j = threadIdx.x; j < R; j += blockDim.x) lambda[j] = sqrt(colsq[j]);
     if (last) {
         for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(FULL, local, o);
         if ((threadIdx.x & 31) == 0) atomicAdd(inner, local);
@@ -354,12 +446,28 @@ size_t ws_layout(spt_tensor t, int R, int ld, Ws *w, void *base) {
     return off;
 }
 
+// Launch shape of gram_kernel for rank R: threads, tile rows, shared memory.
+struct GramShape {
+    int threads, tile_rows;
+    size_t smem;
+};
+GramShape gram_shape(int R) {
+    const int RT = (R + 3) / 4, RP = 4 * RT, team = RT * RT;
+    GramShape g;
+    g.threads = team >= 256 ? team : (256 / team) * team;
+    g.tile_rows = GRAM_ROWS_PER_THREAD * (g.threads / team);
+    g.smem = sizeof(float) * (size_t)g.tile_rows * (RP + 4) + sizeof(double) * (size_t)RP * RP;
+    return g;
+}
+
 template <typename FT>
 spt_status launch_gram(const void *A, int64_t I, int ld, int R, double *G, cudaStream_t st) {
-    const int RT = (R + 3) / 4, team = RT * RT;
-    const int threads = team >= 256 ? team : (256 / team) * team;
-    const size_t smem = sizeof(float) * 32 * (MAXR + 4) + sizeof(double) * (size_t)(RT * 4) * (RT * 4);
-    const int blocks = sm_count() * (threads > 512 ? 1 : 2);
+    const GramShape g = gram_shape(R);
+    const int threads = g.threads;
+    const size_t smem = g.smem;
+    const int64_t tiles = (I + g.tile_rows - 1) / g.tile_rows;
+    const int blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>(tiles, (int64_t)sm_count() * std::max(1, 1024 / threads)));
     gram_kernel<FT><<<blocks, threads, smem, st>>>((const FT *)A, I, ld, R, G);
     SPT_LAUNCH_CHECK("gram_kernel");
     return SPT_OK;
@@ -383,8 +491,9 @@ spt_status ensure_cpals_attrs() {
     SPT_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   sizeof(double) * (MAXR * MAXR + MAXR)));
     SPT_CUDA(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  sizeof(float) * (MAXR * (MAXR + 4) + MAXR * 256)));
-    const size_t gsm = sizeof(float) * 32 * (MAXR + 4) + sizeof(double) * MAXR * MAXR;
+                                  sizeof(float) * (MAXR * (MAXR + 4) + MAXR * 260)));
+    size_t gsm = 0;
+    for (int r = 1; r <= MAXR; ++r) gsm = std::max(gsm, gram_shape(r).smem);
     SPT_CUDA(cudaFuncSetAttribute(gram_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
     SPT_CUDA(cudaFuncSetAttribute(gram_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
     SPT_CUDA(cudaFuncSetAttribute(gram_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
@@ -417,11 +526,12 @@ spt_status enqueue_step(spt_tensor t, void *const *factors, spt_dtype fdt, int R
         SPT_LAUNCH_CHECK("chol_inv_kernel");
         const int CT = (R + 3) / 4;
         const int trows = 4 * (256 / CT);
-        const size_t solve_smem = sizeof(float) * ((size_t)R * CT * 4 + (size_t)R * trows);
+        const size_t solve_smem = sizeof(float) * ((size_t)R * CT * 4 + (size_t)R * (trows + 4));
         const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((In + trows - 1) / trows, sm_count() * 2));
         solve_kernel<<<sblocks, 256, solve_smem, st>>>(w.V, In, ld, R, w.Hinv, w.A32, w.colsq);
         SPT_LAUNCH_CHECK("solve_kernel");
-        const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>((In * ld + 255) / 256, sm_count() * 8));
+        const int rpp = std::max(1, 256 / (ld / 4));  // rows per pass of a 256-thread block
+        const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>((In + rpp - 1) / rpp, sm_count() * 8));
         const int last = (n == d - 1);
         if (fdt == SPT_F32)
             normalize_kernel<float><<<nblocks, 256, 0, st>>>(w.A32, w.V, In, ld, R, w.colsq,
@@ -484,6 +594,7 @@ spt_status cp_als_step(spt_tensor t, void *const *factors, spt_dtype fdt, int ra
     if (!t->coalesced) return fail(SPT_ESTATE, "cp_als_step: the tensor must be created with SPT_COALESCE");
     if (t->d > SPT_MAX_KERNEL_ORDER) return fail(SPT_EUNSUPPORTED, "cp_als_step: order > 5");
     if (rank < 1 || rank > MAXR) return fail(SPT_EUNSUPPORTED, "cp_als_step: rank must be in [1, 128]");
+    if (fdt == SPT_F64) return fail(SPT_EUNSUPPORTED, "cp_als_step: fp64 factors are supported by mttkrp only");
     if (fdt != SPT_F32 && fdt != SPT_BF16 && fdt != SPT_F16) return fail(SPT_EINVAL, "cp_als_step: bad dtype");
     if (ld < rank || ld % 8) return fail(SPT_EINVAL, "cp_als_step: ld must be >= rank and a multiple of 8");
     if ((uintptr_t)workspace & 255) return fail(SPT_EINVAL, "cp_als_step: workspace must be 256-byte aligned");

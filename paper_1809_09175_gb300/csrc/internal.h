@@ -17,14 +17,35 @@ spt_status coalesce_tensor(spt_tensor t, cudaStream_t st);
 spt_status build_perm_mode(spt_tensor t, int n, bool index_only, cudaStream_t st);
 spt_status compute_norm2(spt_tensor t, cudaStream_t st);
 
+// Generalised CP arguments of a gradient launch (see gcp_gradient).
+struct GcpArgs {
+    const void *fac_n;  // A^(n)
+    int loss;
+    double *loss_out;   // nullable
+};
+
 // MTTKRP launch with an explicit (validated) schedule; out is zeroed here.
+// With gcp != NULL the launch runs the generalised CP gradient kernel
+// instead (sorted traversal, one rank block).
 spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt,
-                         int rank, int ld, const float *lambda, float *out,
-                         const spt_schedule &sched, cudaStream_t st);
+                         int rank, int ld, const void *lambda, void *out,
+                         const spt_schedule &sched, cudaStream_t st, const GcpArgs *gcp = nullptr);
 spt_status check_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank,
                           const spt_schedule &s);
 spt_schedule default_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank);
 int elem_bytes(spt_dtype fdt);
+// Bytes of the MTTKRP accumulator and output element (8 for fp64 factors, else 4).
+int acc_bytes(spt_dtype fdt);
+// Per-warp dynamic shared memory of a schedule (barriers, carry, staging).
+size_t schedule_warp_smem(spt_tensor t, const spt_schedule &s, spt_dtype fdt);
+// log2 of the smallest cluster (1, 2, 4 or 8 CTAs) whose shared memory holds
+// the private output copy (ab-byte elements) of a mode of length In next to
+// warp_smem bytes; -1 if none does.
+int private_cluster_log2(int64_t In, int rank, size_t warp_smem, int ab);
+// Candidate schedule q of the tuner's list for rank R, and whether it can run
+// on (tensor, mode) with factors of type fdt.
+spt_schedule candidate(int q, int rank);
+bool candidate_valid(spt_tensor t, int mode, int rank, spt_dtype fdt, const spt_schedule &s, int q);
 // forget the CUDA graphs captured for a tensor (its buffers changed or it died)
 void drop_graphs(spt_tensor t);
 

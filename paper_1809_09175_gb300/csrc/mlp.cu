@@ -256,8 +256,10 @@ spt_status mttkrp_select(spt_tensor t, int mode, spt_dtype fdt, int rank, const 
     if (e != cudaSuccess) return cuda_fail(e, "mttkrp_select");
     spt_schedule cand[SPT_NUM_CANDIDATES];
     int valid[SPT_NUM_CANDIDATES];
-    s = mttkrp_candidates(t, mode, rank, cand, valid);
-    if (s) return s;
+    for (int q = 0; q < SPT_NUM_CANDIDATES; ++q) {
+        cand[q] = candidate(q, rank);
+        valid[q] = candidate_valid(t, mode, rank, fdt, cand[q], q) ? 1 : 0;
+    }
     int bq = -1;
     for (int q = 0; q < SPT_NUM_CANDIDATES; ++q)
         if (valid[q] && (bq < 0 || y[q] < y[bq])) bq = q;

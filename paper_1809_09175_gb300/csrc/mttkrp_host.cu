@@ -7,7 +7,8 @@
 
 namespace spt {
 
-int elem_bytes(spt_dtype fdt) { return fdt == SPT_F32 ? 4 : 2; }
+int elem_bytes(spt_dtype fdt) { return fdt == SPT_F64 ? 8 : (fdt == SPT_F32 ? 4 : 2); }
+int acc_bytes(spt_dtype fdt) { return fdt == SPT_F64 ? 8 : 4; }
 
 namespace {
 int ilog2(int x) {
@@ -42,6 +43,24 @@ spt_status ensure_smem_attr(MttkrpKernelFn fn, int smem) {
 }
 }  // namespace
 
+size_t schedule_warp_smem(spt_tensor t, const spt_schedule &s, spt_dtype fdt) {
+    const int G = 32 / s.lanes_per_nnz;
+    const int npw = G * adjust_S(s.nnz_per_group, G);
+    const int wpe = s.scatter == SPT_SCATTER_PERM     ? 1
+                    : s.scatter == SPT_SCATTER_SORTED ? record_words(t->d)
+                                                      : t->d + 1;
+    return warp_smem_bytes(s.warps_per_cta, s.chunks, s.lanes_per_nnz, acc_bytes(fdt), wpe, npw);
+}
+
+int private_cluster_log2(int64_t In, int rank, size_t warp_smem, int ab) {
+    const size_t pld = (size_t)((rank + 3) & ~3);
+    for (int k = 0; k <= 3; ++k) {
+        const size_t rows = (size_t)((In + (1 << k) - 1) >> k);
+        if (warp_smem + rows * pld * ab <= 227 * 1024) return k;
+    }
+    return -1;
+}
+
 spt_schedule default_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank) {
     if (t->pref_set[mode] && t->pref_rank[mode] == rank && t->pref_fdt[mode] == fdt &&
         check_schedule(t, mode, fdt, rank, t->pref[mode]) == SPT_OK)
@@ -59,7 +78,7 @@ spt_schedule default_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank) {
     // carry), so four 8-warp CTAs fit an SM; at most 256 nonzeros per chunk
     const int narr = s.scatter == SPT_SCATTER_PERM ? 1
                      : (s.scatter == SPT_SCATTER_SORTED ? record_words(t->d) : t->d + 1);
-    const int npw = std::min(256, (7168 - 16 - carry_bytes(s.chunks, lanes)) / (8 * narr));
+    const int npw = std::min(256, (7168 - 16 - carry_bytes(s.chunks, lanes, acc_bytes(fdt))) / (8 * narr));
     s.nnz_per_group = std::max(4, npw / (32 / lanes));
     s.warps_per_cta = 8;
     s.ctas_per_sm = 0;
@@ -68,8 +87,7 @@ spt_schedule default_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank) {
 
 spt_status check_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank, const spt_schedule &s) {
     (void)fdt;
-    (void)rank;
-    if (s.scatter < SPT_SCATTER_ATOMIC || s.scatter > SPT_SCATTER_SORTED)
+    if (s.scatter < SPT_SCATTER_ATOMIC || s.scatter > SPT_SCATTER_PRIVATE)
         return fail(SPT_EINVAL, "schedule: unknown scatter strategy");
     if (!pow2_in(s.lanes_per_nnz, 1, 32)) return fail(SPT_EINVAL, "schedule: lanes_per_nnz must be 1,2,4,..,32");
     if (s.chunks < 1 || s.chunks > 2) return fail(SPT_EINVAL, "schedule: chunks must be 1 or 2");
@@ -80,12 +98,16 @@ spt_status check_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank, const
         return fail(SPT_ESTATE, "schedule: permuted traversal needs build_mode_permutation(mode)");
     if (s.scatter == SPT_SCATTER_SORTED && !t->sorted_buf[mode])
         return fail(SPT_ESTATE, "schedule: sorted traversal needs the mode-sorted copy");
+    if (s.scatter == SPT_SCATTER_PRIVATE &&
+        private_cluster_log2(t->dims[mode], rank, schedule_warp_smem(t, s, fdt), acc_bytes(fdt)) < 0)
+        return fail(SPT_EINVAL, "schedule: the private scatter's copy of this mode's output does not fit "
+                                "the shared memory of a cluster of 8 CTAs");
     return SPT_OK;
 }
 
 spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt,
-                         int rank, int ld, const float *lambda, float *out,
-                         const spt_schedule &s, cudaStream_t st) {
+                         int rank, int ld, const void *lambda, void *out,
+                         const spt_schedule &s, cudaStream_t st, const GcpArgs *gcp) {
     const int vec = 4;  // columns per lane chunk
     const int L = s.lanes_per_nnz, C = s.chunks;
     const int G = 32 / L;
@@ -93,12 +115,15 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
     const int S = adjust_S(s.nnz_per_group, G);
     const int npw = G * S;
     const int wpc = s.warps_per_cta;
-    SPT_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)t->dims[mode] * ld, st));
+    const int ab = acc_bytes(fdt);
+    SPT_CUDA(cudaMemsetAsync(out, 0, (size_t)ab * (size_t)t->dims[mode] * ld, st));
     if (t->nnz == 0) return SPT_OK;
 
     const int D1 = t->d - 1;
-    const int kmode = s.scatter == SPT_SCATTER_ATOMIC ? M_ATOMIC
-                      : (s.scatter == SPT_SCATTER_SORTED ? M_SORTED : M_PERM);
+    const int kmode = s.scatter == SPT_SCATTER_ATOMIC    ? M_ATOMIC
+                      : s.scatter == SPT_SCATTER_SORTED  ? M_SORTED
+                      : s.scatter == SPT_SCATTER_PRIVATE ? M_PRIVATE
+                                                         : M_PERM;
     MttkrpParams p{};
     p.rows = t->idx[mode];
     p.vals = t->vals;
@@ -124,18 +149,65 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
     p.npw = npw;
     p.nchunks = (t->nnz + npw - 1) / npw;
     p.err = t->dev_err;
+    p.loss = -1;
+    if (gcp) {
+        if (kmode != M_SORTED || p.n_rb != 1)
+            return fail(SPT_EINVAL, "gcp: needs the sorted traversal and one rank block covering the rank");
+        p.fac_n = gcp->fac_n;
+        p.loss = gcp->loss;
+        p.loss_out = gcp->loss_out;
+    }
 
     const int wpe = kmode == M_PERM ? 1 : (kmode == M_SORTED ? record_words(t->d) : D1 + 2);
-    const size_t smem = 16 * (size_t)wpc + (size_t)wpc * carry_bytes(C, L) + (size_t)wpc * 2 * wpe * npw * 4;
+    size_t smem = warp_smem_bytes(wpc, C, L, ab, wpe, npw);
     if (smem > 227 * 1024)
         return fail(SPT_EINVAL, "schedule: staging buffers exceed 227 KB of shared memory "
                                 "(lower warps_per_cta or nnz_per_group)");
-    MttkrpKernelFn fn = fdt == SPT_F32    ? mttkrp_kernel_f32(C, D1, kmode)
+    int K = 1;
+    if (kmode == M_PRIVATE) {
+        const int log2K = private_cluster_log2(t->dims[mode], rank, smem, ab);
+        if (log2K < 0)
+            return fail(SPT_EINVAL, "schedule: the private scatter's copy of this mode's output does not fit "
+                                    "the shared memory of a cluster of 8 CTAs");
+        K = 1 << log2K;
+        p.In = (int)t->dims[mode];
+        p.pld = (rank + 3) & ~3;
+        p.log2K = log2K;
+        p.prows = (int)((t->dims[mode] + K - 1) / K);
+        smem += (size_t)p.prows * p.pld * ab;
+    }
+    MttkrpKernelFn fn = gcp               ? gcp_kernel_fn(fdt, C, D1)
+                        : fdt == SPT_F32  ? mttkrp_kernel_f32(C, D1, kmode)
                         : fdt == SPT_BF16 ? mttkrp_kernel_bf16(C, D1, kmode)
+                        : fdt == SPT_F64  ? mttkrp_kernel_f64(C, D1, kmode)
                                           : mttkrp_kernel_f16(C, D1, kmode);
     if (!fn) return fail(SPT_EUNSUPPORTED, "mttkrp: no kernel for this order/chunks");
     spt_status e = ensure_smem_attr(fn, (int)smem);
     if (e) return e;
+    if (K > 1) {
+        // clusters of K CTAs; a persistent grid of as many clusters as fit at once
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = K;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(wpc * 32);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(K * sm_count());
+        int ncl = 0;
+        SPT_CUDA(cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg));
+        if (ncl < 1) return fail(SPT_EINVAL, "schedule: a cluster of the private scatter does not fit the GPU");
+        const int64_t need_cl = ((p.nchunks + wpc - 1) / wpc + K - 1) / K;
+        const int cl = (int)std::max<int64_t>(1, std::min<int64_t>(ncl, need_cl));
+        cfg.gridDim = dim3(cl * K);
+        SPT_CUDA(cudaLaunchKernelEx(&cfg, fn, p));
+        SPT_LAUNCH_CHECK("mttkrp_kernel cluster launch");
+        return SPT_OK;
+    }
     int bps = 0;
     SPT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, wpc * 32, smem));
     if (bps < 1) return fail(SPT_EINVAL, "schedule: kernel does not fit on an SM");

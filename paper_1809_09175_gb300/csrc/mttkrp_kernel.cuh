@@ -1,9 +1,9 @@
-// mttkrp_kernel.cuh -- the sparse COO MTTKRP kernel (Sec. 2 eq. mttkrp).
+// mttkrp_kernel.cuh -- the sparse COO MTTKRP kernel (Sec. 3 eq. mttkrp).
 //
 //   out(k, j) = lambda_j * sum_{i : l_in = k} x_i * prod_{m != n} A^(m)(l_im, j)
 //
 // Work decomposition (GB300 mapping of the paper's league/team/vector levels,
-// Sec. 3 Tab. "Levels of Parallelism"):
+// Sec. 4 Tab. "Levels of Parallelism"):
 //  * Each warp of a persistent grid owns a contiguous range of chunks of
 //    `npw` consecutive nonzeros of the traversal order.  A chunk's
 //    nonzeros are staged into the warp's shared memory with 1-D bulk copies
@@ -29,10 +29,19 @@
 //                For both, a group writes a finished row with a plain store;
 //                the first and last run of every group are combined across
 //                the warp with shuffles (a segmented reduction over the
-//                groups), and the last open run is carried in registers into
-//                the warp's next chunk, so only the first and last row of the
-//                warp's whole range are added atomically: only those rows can
-//                be shared with other warps.
+//                groups), and the last open run is carried in shared memory
+//                into the warp's next chunk, so only the first and last row
+//                of the warp's whole range are added atomically: only those
+//                rows can be shared with other warps.
+//      M_PRIVATE storage order like M_ATOMIC, but every row flush is an
+//                atomic add into a private copy of the output held in shared
+//                memory (the privatised scatter the paper proposes for short
+//                modes, Sec. 8).  When one CTA's shared memory cannot hold
+//                I_n rows, a thread-block cluster of K CTAs splits them
+//                (row k lives in CTA k mod K, local row k / K) and adds reach
+//                the owner through distributed shared memory.  After the
+//                cluster barrier each CTA adds its rows to the output with
+//                16-byte vector atomics.
 //  * Columns: rank block rb covers columns [rb*L*C*VEC, ...); lane l's chunk
 //    c starts at column rb*L*C*VEC + (c*L + l)*VEC.  Columns >= R are
 //    computed from the factors' padding and written as zeros.
@@ -41,7 +50,7 @@
 
 namespace spt {
 
-enum MttkrpMode { M_ATOMIC = 0, M_SORTED = 1, M_PERM = 2 };
+enum MttkrpMode { M_ATOMIC = 0, M_SORTED = 1, M_PERM = 2, M_PRIVATE = 3 };
 
 // Words of one packed record of the mode-sorted copy: {row, d-1 other
 // coordinates, value} = d+1 words, padded to 2, 4 or 6 for vector loads.
@@ -57,8 +66,8 @@ struct MttkrpParams {
     const int32_t *rec;      // M_SORTED: packed records in mode-n order
     const void *fac[4];      // factor matrices of the other modes
     int fld;                 // factor row stride (elements)
-    const float *lambda;     // nullable
-    float *out;              // I_n x old, zeroed before launch
+    const void *lambda;      // nullable; accumulator type (float, double for fp64)
+    void *out;               // I_n x old accumulator type (float, double for fp64), zeroed first
     int64_t old;
     int64_t nnz;
     int R;
@@ -69,6 +78,15 @@ struct MttkrpParams {
     int npw;      // nonzeros per warp chunk = (32 >> log2L) * S, a multiple of 4
     int64_t nchunks;
     int *err;     // device status word
+    // M_PRIVATE: the private output copy in shared memory
+    int In;       // rows of the output (mode length)
+    int pld;      // private row stride in accumulator elements, R rounded up to 4
+    int log2K;    // cluster size K = 1 << log2K CTAs share the rows
+    int prows;    // private rows per CTA = ceil(In / K)
+    // generalised CP gradient (gcp kernels only)
+    const void *fac_n;   // the mode's own factor A^(n): the model value needs it
+    int loss;            // 0 Poisson (stored part), 1 Bernoulli-logit, 2 Gaussian
+    double *loss_out;    // nullable: sum of the stored entries' loss terms
 };
 
 __device__ __forceinline__ uint4 ldg16(const void *p) {
@@ -78,21 +96,34 @@ __device__ __forceinline__ uint4 ldg16(const void *p) {
 __device__ __forceinline__ void red_add4(float *dst, const float *v) {
     atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(v[0], v[1], v[2], v[3]));
 }
+__device__ __forceinline__ void red_add4(double *dst, const double *v) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) atomicAdd(dst + q, v[q]);
+}
+__device__ __forceinline__ float fma_acc(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_acc(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ void store4(float *dst, const float *v) {
+    *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double *dst, const double *v) {
+    reinterpret_cast<double2 *>(dst)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(dst)[1] = make_double2(v[2], v[3]);
+}
 
 // Register cap: small column blocks fit two 512-thread CTAs (<= 64 registers).
 #ifndef SPT_MTTKRP_MINBLOCKS
 #define SPT_MTTKRP_MINBLOCKS 2
 #endif
 template <typename FT, int C> struct MinBlocks {
-    static constexpr int value = (Elem<FT>::VEC * C <= 4) ? SPT_MTTKRP_MINBLOCKS : 1;
+    static constexpr int value = (Elem<FT>::VEC * C <= 4 && Elem<FT>::BYTES <= 4) ? SPT_MTTKRP_MINBLOCKS : 1;
 };
 
 // Open row sum carried from one chunk to the next by a warp that walks a
 // contiguous range of chunks (one rank block), kept in the warp's shared
 // memory between chunks: a 16-byte header (the carried row, then the first
-// and last row of the warp's range) and C x 4 floats for each of the L column
-// slices (every group holds the same slices).
-__host__ __device__ constexpr int carry_bytes(int C, int L) { return 16 + 16 * C * L; }
+// and last row of the warp's range) and C x 4 accumulators of AB bytes for
+// each of the L column slices (every group holds the same slices).
+__host__ __device__ constexpr int carry_bytes(int C, int L, int AB) { return 16 + 4 * AB * C * L; }
 
 // First and last mode-n coordinate of the staged chunk.
 template <int D1, int MODE>
@@ -117,15 +148,20 @@ __device__ __forceinline__ void chunk_bounds(const MttkrpParams &p, const int32_
 // chunk's last open run is handed over instead of written, the carried run of
 // the previous chunk joins this chunk's first run, and the shared rows are the
 // range's first and last rows from the carry header.
-template <typename FT, int C, int D1, int MODE>
+template <typename FT, int C, int D1, int MODE, bool GCP = false>
 __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_t *buf, int n, int b0,
-                                             int b1, unsigned char *carry) {
+                                             int b1, unsigned char *carry, typename Elem<FT>::Acc *priv,
+                                             double *lacc = nullptr) {
     using E = Elem<FT>;
     using Raw = typename E::Raw;
+    using AT = typename E::Acc;
     constexpr int VEC = E::VEC;
     constexpr int DA = D1 > 0 ? D1 : 1;
+    // gathered rows per nonzero: the d-1 other factors, plus the own factor's
+    // row for the generalised CP model value (slot D1)
+    constexpr int NR = GCP ? D1 + 1 : DA;
     constexpr int REC = record_words(D1 + 1);
-    constexpr int LOADS = D1 * C;
+    constexpr int LOADS = NR * C;
     constexpr int U = (LOADS <= 2) ? 2 : 1;
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -143,51 +179,68 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
 
     for (int rb = 0; rb < p.n_rb; ++rb) {
         int col[C], nv[C];
-        float lam[C][VEC];
-        const char *fb[DA][C];  // this lane's column chunk of each factor
+        AT lam[C][VEC];
+        const char *fb[NR][C];  // this lane's column chunk of each factor
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             col[c] = rb * p.rb_cols + (c * L + l) * VEC;
             nv[c] = max(0, min(VEC, p.R - col[c]));
 #pragma unroll
             for (int v = 0; v < VEC; ++v)
-                lam[c][v] = (p.lambda && v < nv[c]) ? __ldg(p.lambda + col[c] + v) : 1.0f;
+                lam[c][v] = (p.lambda && v < nv[c]) ? __ldg(reinterpret_cast<const AT *>(p.lambda) + col[c] + v)
+                                                     : (AT)1;
 #pragma unroll
             for (int m = 0; m < D1; ++m)
                 fb[m][c] = reinterpret_cast<const char *>(p.fac[m]) + (int64_t)col[c] * sizeof(FT);
+            if (GCP) fb[NR - 1][c] = reinterpret_cast<const char *>(p.fac_n) + (int64_t)col[c] * sizeof(FT);
         }
 
-        float acc[C][VEC], facc[C][VEC];
+        AT acc[C][VEC], facc[C][VEC];
 #pragma unroll
         for (int c = 0; c < C; ++c)
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[c][v] = facc[c][v] = 0.0f;
+            for (int v = 0; v < VEC; ++v) acc[c][v] = facc[c][v] = (AT)0;
         int cur = -1, frow = -1;
         bool fclosed = false;
 
         // emit a finished row sum: atomic for shared rows, plain store otherwise
-        auto write_row = [&](int row, float (&a)[C][VEC], bool atomic) {
-            float *dst = p.out + (int64_t)row * p.old;
+        auto write_row = [&](int row, AT (&a)[C][VEC], bool atomic) {
+            if (MODE == M_PRIVATE) {  // add into the owning CTA's private copy
+                const int K = 1 << p.log2K;
+                AT *prow = priv + (int64_t)(row >> p.log2K) * p.pld;
+                const uint32_t owner = (uint32_t)(row & (K - 1));
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        if (v >= nv[c]) continue;
+                        const AT w = a[c][v] * lam[c][v];
+                        const uint32_t a = smem_u32(prow + col[c] + v);
+                        if (K == 1)
+                            red_add_shared(a, w);
+                        else
+                            red_add_cluster(mapa_shared(a, owner), w);
+                    }
+                }
+                return;
+            }
+            AT *dst = reinterpret_cast<AT *>(p.out) + (int64_t)row * p.old;
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 if (nv[c] == 0) continue;
-                float w[VEC];  // columns >= R hold padding products: write zeros
+                AT w[VEC];  // columns >= R hold padding products: write zeros
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) w[v] = v < nv[c] ? a[c][v] * lam[c][v] : 0.0f;
-                if (atomic) {
+                for (int v = 0; v < VEC; ++v) w[v] = v < nv[c] ? a[c][v] * lam[c][v] : (AT)0;
 #pragma unroll
-                    for (int q = 0; q < VEC; q += 4) red_add4(dst + col[c] + q, w + q);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < VEC; q += 4)
-                        *reinterpret_cast<float4 *>(dst + col[c] + q) =
-                            make_float4(w[q], w[q + 1], w[q + 2], w[q + 3]);
+                for (int q = 0; q < VEC; q += 4) {
+                    if (atomic) red_add4(dst + col[c] + q, w + q);
+                    else store4(dst + col[c] + q, w + q);
                 }
             }
         };
 
         // load one nonzero's row, value and its d-1 factor-row chunks
-        auto fetch = [&](int e, int &row, float &x, Raw (&rw)[DA][C]) {
+        auto fetch = [&](int e, int &row, float &x, Raw (&rw)[NR][C]) {
             int r[DA];
             if (MODE == M_SORTED) {
                 int w[REC];
@@ -225,29 +278,77 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
                 for (int c = 0; c < C; ++c)
                     rw[m][c] = nv[c] > 0 ? E::load(fb[m][c] + (int64_t)r[m] * rstride) : Raw{};
             }
+            if (GCP) {
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    rw[NR - 1][c] = nv[c] > 0 ? E::load(fb[NR - 1][c] + (int64_t)row * rstride) : Raw{};
+            }
         };
         // multiply out one nonzero and fold it into the running row sum;
         // `vote`: every lane of the warp runs this step (uniform fast path)
-        auto step = [&](int row, float x, const Raw (&rw)[DA][C], bool vote) {
-            float part[C][VEC], fl[C][VEC];  // x * first D1-1 factors; last factor
+        auto step = [&](int row, float x, const Raw (&rw)[NR][C], bool vote) {
+            AT part[C][VEC], fl[C][VEC];  // x * first D1-1 factors; last factor
+            if constexpr (GCP) {
+                // t = prod of the other factors' rows; m = <A^(n)(row,:), t>
+                // summed over the group's lanes; the row sum gathers
+                // df/dm(x, m) * t (part = df/dm, fl = t)
+                AT dot = (AT)0;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) fl[c][v] = (AT)1;
+#pragma unroll
+                    for (int m = 0; m < D1; ++m) {
+                        AT f[VEC];
+                        E::widen(rw[m][c], f);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) fl[c][v] *= f[v];
+                    }
+                    AT an[VEC];
+                    E::widen(rw[NR - 1][c], an);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v)
+                        if (v < nv[c]) dot = fma_acc(fl[c][v], an[v], dot);
+                }
+                const unsigned gmask = L == 32 ? FULL : (((1u << L) - 1u) << (g * L));
+                for (int o = 1; o < L; o <<= 1) dot += __shfl_xor_sync(gmask, dot, o);
+                const float mv = (float)dot;
+                float y, fv;
+                if (p.loss == 0) {  // Poisson: the stored entry's part of 1 - x/m
+                    y = -x / mv;
+                    fv = -x * logf(mv);
+                } else if (p.loss == 1) {  // Bernoulli, logit link
+                    y = 1.0f / (1.0f + expf(-mv)) - x;
+                    fv = (mv > 0.0f ? mv + log1pf(expf(-mv)) : log1pf(expf(mv))) - x * mv;
+                } else {  // Gaussian
+                    y = 2.0f * (mv - x);
+                    fv = (mv - x) * (mv - x);
+                }
+                if (l == 0) *lacc += (double)fv;
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) part[c][v] = (AT)y;
+            } else {
 #pragma unroll
             for (int c = 0; c < C; ++c) {
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) part[c][v] = x;
+                for (int v = 0; v < VEC; ++v) part[c][v] = (AT)x;
 #pragma unroll
                 for (int m = 0; m + 1 < D1; ++m) {
-                    float f[VEC];
+                    AT f[VEC];
                     E::widen(rw[m][c], f);
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) part[c][v] *= f[v];
                 }
                 if (D1 > 0) E::widen(rw[DA - 1][c], fl[c]);
             }
+            }
             const bool ch = row != cur;
             const bool any = vote ? __any_sync(FULL, ch) : ch;
             if (any && ch) {
                 if (cur >= 0) {
-                    if (MODE == M_ATOMIC) {
+                    if (MODE == M_ATOMIC || MODE == M_PRIVATE) {
                         write_row(cur, acc, true);
                     } else if (!fclosed) {
                         fclosed = true;
@@ -271,7 +372,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
                 for (int c = 0; c < C; ++c)
 #pragma unroll
                     for (int v = 0; v < VEC; ++v)
-                        acc[c][v] = D1 > 0 ? fmaf(part[c][v], fl[c][v], acc[c][v])
+                        acc[c][v] = D1 > 0 ? fma_acc(part[c][v], fl[c][v], acc[c][v])
                                            : acc[c][v] + part[c][v];
             }
         };
@@ -282,7 +383,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
             for (; t + U <= S; t += U) {
                 int rowu[U];
                 float xu[U];
-                Raw raw[U][DA][C];
+                Raw raw[U][NR][C];
 #pragma unroll
                 for (int u = 0; u < U; ++u) fetch(e0 + t + u, rowu[u], xu[u], raw[u]);
 #pragma unroll
@@ -291,7 +392,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
             for (; t < S; ++t) {
                 int row;
                 float x;
-                Raw rw[DA][C];
+                Raw rw[NR][C];
                 fetch(e0 + t, row, x, rw);
                 step(row, x, rw, true);
             }
@@ -300,28 +401,28 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
             for (int t = 0; t < cnt; ++t) {
                 int row;
                 float x;
-                Raw rw[DA][C];
+                Raw rw[NR][C];
                 fetch(e0 + t, row, x, rw);
                 step(row, x, rw, false);
             }
         }
 
-        if (MODE == M_ATOMIC) {
+        if (MODE == M_ATOMIC || MODE == M_PRIVATE) {
             if (cur >= 0) write_row(cur, acc, true);
         } else {
             // Segmented combine of the groups' open runs, in group order.
             // Every lane tracks the running (orow, oacc) for its columns;
             // group 0's lanes perform the writes.
             int *crow_p = reinterpret_cast<int *>(carry);
-            float *cacc_p = carry ? reinterpret_cast<float *>(carry + 16) + l * (C * VEC) : nullptr;
-            float oacc[C][VEC];
+            AT *cacc_p = carry ? reinterpret_cast<AT *>(carry + 16) + l * (C * VEC) : nullptr;
+            AT oacc[C][VEC];
 #pragma unroll
             for (int c = 0; c < C; ++c)
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) oacc[c][v] = carry ? cacc_p[c * VEC + v] : 0.0f;
+                for (int v = 0; v < VEC; ++v) oacc[c][v] = carry ? cacc_p[c * VEC + v] : (AT)0;
             int orow = carry ? *crow_p : -1;
             const bool writer = (g == 0);
-            auto emit = [&](int row, float (&a)[C][VEC]) {
+            auto emit = [&](int row, AT (&a)[C][VEC]) {
                 if (writer) {
                     const int s0 = carry ? crow_p[1] : b0, s1 = carry ? crow_p[2] : b1;
                     write_row(row, a, row == s0 || row == s1);
@@ -333,7 +434,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
                 if (scur < 0) break;  // this and later groups got no nonzeros
                 const int sfc = __shfl_sync(FULL, (int)fclosed, srcl);
                 const int sfrow = __shfl_sync(FULL, frow, srcl);
-                float F[C][VEC], A[C][VEC];
+                AT F[C][VEC], A[C][VEC];
 #pragma unroll
                 for (int c = 0; c < C; ++c)
 #pragma unroll
@@ -390,41 +491,58 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
 template <typename FT, int C>
 __device__ __forceinline__ void flush_carry(const MttkrpParams &p, const unsigned char *carry) {
     constexpr int VEC = Elem<FT>::VEC;
+    using AT = typename Elem<FT>::Acc;
     const int lane = threadIdx.x & 31;
     const int L = 1 << p.log2L;
     const int row = *reinterpret_cast<const int *>(carry);
     if ((lane >> p.log2L) != 0 || row < 0) return;  // group 0 writes
     const int l = lane & (L - 1);
-    const float *acc = reinterpret_cast<const float *>(carry + 16) + l * (C * VEC);
-    float *dst = p.out + (int64_t)row * p.old;
+    const AT *acc = reinterpret_cast<const AT *>(carry + 16) + l * (C * VEC);
+    AT *dst = reinterpret_cast<AT *>(p.out) + (int64_t)row * p.old;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const int col = (c * L + l) * VEC;
         const int nv = max(0, min(VEC, p.R - col));
         if (nv == 0) continue;
-        float w[VEC];
+        AT w[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v)
-            w[v] = v < nv ? acc[c * VEC + v] * (p.lambda ? __ldg(p.lambda + col + v) : 1.0f) : 0.0f;
+            w[v] = v < nv ? acc[c * VEC + v] * (p.lambda ? __ldg(reinterpret_cast<const AT *>(p.lambda) + col + v)
+                                                          : (AT)1)
+                          : (AT)0;
 #pragma unroll
         for (int q = 0; q < VEC; q += 4) red_add4(dst + col + q, w + q);
     }
 }
 
-template <typename FT, int C, int D1, int MODE>
-__global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(const MttkrpParams p) {
+// Staged 32-bit words per nonzero of a traversal mode.
+template <int D1, int MODE> struct Staging {
+    static constexpr int NARR = (MODE == M_PERM) ? 1 : (D1 + 2);  // SoA arrays staged
+    static constexpr int WPE = (MODE == M_SORTED) ? record_words(D1 + 1) : NARR;
+};
+
+// Bytes of the per-warp part of the dynamic shared memory (barriers, run
+// carry, two staging buffers); the private output copy follows them.
+__host__ __device__ inline size_t warp_smem_bytes(int wpc, int C, int L, int AB, int wpe, int npw) {
+    return 16 * (size_t)wpc + (size_t)wpc * carry_bytes(C, L, AB) + (size_t)wpc * 2 * wpe * npw * 4;
+}
+
+// One warp's contiguous range of chunks: stage, compute, hand the run carry on.
+template <typename FT, int C, int D1, int MODE, bool GCP = false>
+__device__ __forceinline__ void mttkrp_warp_range(const MttkrpParams &p, unsigned char *smem_raw,
+                                                  typename Elem<FT>::Acc *priv) {
+    using AT = typename Elem<FT>::Acc;
     constexpr int REC = record_words(D1 + 1);
-    constexpr int NARR = (MODE == M_PERM) ? 1 : (D1 + 2);          // SoA arrays staged
-    constexpr int WPE = (MODE == M_SORTED) ? REC : NARR;             // staged words / nonzero
+    constexpr int NARR = Staging<D1, MODE>::NARR;
+    constexpr int WPE = Staging<D1, MODE>::WPE;
     constexpr unsigned FULL = 0xffffffffu;
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpc = blockDim.x >> 5;
     const int npw = p.npw;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw) + 2 * warp;
-    const int cb = carry_bytes(C, 1 << p.log2L);
+    const int cb = carry_bytes(C, 1 << p.log2L, (int)sizeof(AT));
     unsigned char *carry = smem_raw + 16 * wpc + (size_t)warp * cb;
     int32_t *wbuf = reinterpret_cast<int32_t *>(smem_raw + 16 * wpc + (size_t)wpc * cb) +
                     (size_t)warp * 2 * WPE * npw;
@@ -483,7 +601,7 @@ __global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(co
 
     // Sorted traversals with one rank block carry the open run across the
     // range's chunks; only the range's first and last rows are then shared.
-    const bool use_carry = (MODE != M_ATOMIC) && p.n_rb == 1;
+    const bool use_carry = (MODE == M_SORTED || MODE == M_PERM) && p.n_rb == 1;
     if (use_carry) {
         const int64_t e_first = (int64_t)ch_begin * npw;
         const int64_t e_last = ((int64_t)ch_end * npw < p.nnz ? (int64_t)ch_end * npw : p.nnz) - 1;
@@ -499,13 +617,14 @@ __global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(co
             }
         }
         if ((lane >> p.log2L) == 0) {
-            float *ca = reinterpret_cast<float *>(carry + 16) + lane * (C * Elem<FT>::VEC);
+            AT *ca = reinterpret_cast<AT *>(carry + 16) + lane * (C * Elem<FT>::VEC);
 #pragma unroll
-            for (int q = 0; q < C * Elem<FT>::VEC; ++q) ca[q] = 0.0f;
+            for (int q = 0; q < C * Elem<FT>::VEC; ++q) ca[q] = (AT)0;
         }
         __syncwarp();
     }
 
+    double lacc = 0.0;  // generalised CP: this lane's sum of loss terms
     int k = 0;
     for (int ch = ch_begin; ch < ch_end; ++ch, ++k) {
         const int s = k & 1;
@@ -534,11 +653,11 @@ __global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(co
         __syncwarp();
 
         if (use_carry) {
-            mttkrp_chunk<FT, C, D1, MODE>(p, buf, n, -1, -1, carry);
+            mttkrp_chunk<FT, C, D1, MODE, GCP>(p, buf, n, -1, -1, carry, nullptr, &lacc);
         } else {
             int b0, b1;
             chunk_bounds<D1, MODE>(p, buf, n, b0, b1);
-            mttkrp_chunk<FT, C, D1, MODE>(p, buf, n, b0, b1, nullptr);
+            mttkrp_chunk<FT, C, D1, MODE, GCP>(p, buf, n, b0, b1, nullptr, priv, &lacc);
         }
 
         __syncwarp();  // every lane is done with this stage before it is refilled
@@ -551,30 +670,89 @@ __global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(co
         __syncwarp();
         flush_carry<FT, C>(p, carry);
     }
+    if (GCP && p.loss_out) {
+        for (int o = 16; o > 0; o >>= 1) lacc += __shfl_xor_sync(FULL, lacc, o);
+        if (lane == 0) atomicAdd(p.loss_out, lacc);
+    }
+}
+
+// Generalised CP gradient over the mode-sorted copy: the MTTKRP traversal
+// with each nonzero's value replaced by df/dm at the model value m.
+template <typename FT, int C, int D1>
+__global__ void __launch_bounds__(512, 1) gcp_kernel(const MttkrpParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    mttkrp_warp_range<FT, C, D1, M_SORTED, true>(p, smem_raw, nullptr);
+}
+
+// Add this CTA's private rows (row = local * K + cluster rank) to the output
+// with vector atomics (16 bytes for float), skipping all-zero quads.
+template <typename AT>
+__device__ __forceinline__ void flush_private(const MttkrpParams &p, const AT *priv, int rank) {
+    const int q4 = p.pld >> 2;
+    const int64_t total = (int64_t)p.prows * q4;
+    for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+        const int lr = (int)(i / q4);
+        const int c4 = (int)(i - (int64_t)lr * q4);
+        const int row = (lr << p.log2K) + rank;
+        if (row >= p.In) continue;
+        const AT *src = priv + (int64_t)lr * p.pld + 4 * c4;
+        const AT v[4] = {src[0], src[1], src[2], src[3]};
+        if (v[0] != (AT)0 || v[1] != (AT)0 || v[2] != (AT)0 || v[3] != (AT)0)
+            red_add4(reinterpret_cast<AT *>(p.out) + (int64_t)row * p.old + 4 * c4, v);
+    }
+}
+
+template <typename FT, int C, int D1, int MODE>
+__global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(const MttkrpParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (MODE != M_PRIVATE) {
+        mttkrp_warp_range<FT, C, D1, MODE>(p, smem_raw, nullptr);
+        return;
+    }
+    // Privatised scatter: zero this CTA's rows, wait until every CTA of the
+    // cluster has (remote adds may follow at once), accumulate, wait until
+    // every add of the cluster has landed, then flush.  Every thread reaches
+    // both barriers: warps without chunks skip straight to them.
+    using AT = typename Elem<FT>::Acc;
+    const int wpc = blockDim.x >> 5;
+    AT *priv = reinterpret_cast<AT *>(smem_raw + warp_smem_bytes(wpc, C, 1 << p.log2L, (int)sizeof(AT),
+                                                                 Staging<D1, MODE>::WPE, p.npw));
+    const int nfl = p.prows * p.pld;  // a multiple of 4
+    const AT zero4[4] = {(AT)0, (AT)0, (AT)0, (AT)0};
+    for (int i = 4 * threadIdx.x; i < nfl; i += 4 * blockDim.x) store4(priv + i, zero4);
+    const bool clustered = p.log2K > 0;
+    if (clustered) cluster_sync_all(); else __syncthreads();
+    mttkrp_warp_range<FT, C, D1, MODE>(p, smem_raw, priv);
+    __syncwarp();  // the warp is converged for the aligned cluster barrier
+    if (clustered) cluster_sync_all(); else __syncthreads();
+    flush_private(p, priv, clustered ? (int)cluster_ctarank() : 0);
 }
 
 typedef void (*MttkrpKernelFn)(const MttkrpParams);
 
-// Kernel table of one element type: fn(C in {1,2}, D1 in 0..4, mode in 0..2).
+// Kernel table of one element type: fn(C in {1,2}, D1 in 0..4, mode in 0..3).
 MttkrpKernelFn mttkrp_kernel_f32(int C, int D1, int mode);
 MttkrpKernelFn mttkrp_kernel_bf16(int C, int D1, int mode);
 MttkrpKernelFn mttkrp_kernel_f16(int C, int D1, int mode);
+MttkrpKernelFn mttkrp_kernel_f64(int C, int D1, int mode);
+// Generalised CP gradient kernels: fdt in {F32, BF16, F16}, C in {1,2}, D1 in 1..4.
+MttkrpKernelFn gcp_kernel_fn(spt_dtype fdt, int C, int D1);
 
-#define SPT_INSTANTIATE_MTTKRP_TABLE(FT, NAME)                                            \
-    MttkrpKernelFn NAME(int C, int D1, int mode) {                                       \
-        static const MttkrpKernelFn tab[2][5][3] = {                                     \
-            {{mttkrp_kernel<FT, 1, 0, 0>, mttkrp_kernel<FT, 1, 0, 1>, mttkrp_kernel<FT, 1, 0, 2>}, \
-             {mttkrp_kernel<FT, 1, 1, 0>, mttkrp_kernel<FT, 1, 1, 1>, mttkrp_kernel<FT, 1, 1, 2>}, \
-             {mttkrp_kernel<FT, 1, 2, 0>, mttkrp_kernel<FT, 1, 2, 1>, mttkrp_kernel<FT, 1, 2, 2>}, \
-             {mttkrp_kernel<FT, 1, 3, 0>, mttkrp_kernel<FT, 1, 3, 1>, mttkrp_kernel<FT, 1, 3, 2>}, \
-             {mttkrp_kernel<FT, 1, 4, 0>, mttkrp_kernel<FT, 1, 4, 1>, mttkrp_kernel<FT, 1, 4, 2>}}, \
-            {{mttkrp_kernel<FT, 2, 0, 0>, mttkrp_kernel<FT, 2, 0, 1>, mttkrp_kernel<FT, 2, 0, 2>}, \
-             {mttkrp_kernel<FT, 2, 1, 0>, mttkrp_kernel<FT, 2, 1, 1>, mttkrp_kernel<FT, 2, 1, 2>}, \
-             {mttkrp_kernel<FT, 2, 2, 0>, mttkrp_kernel<FT, 2, 2, 1>, mttkrp_kernel<FT, 2, 2, 2>}, \
-             {mttkrp_kernel<FT, 2, 3, 0>, mttkrp_kernel<FT, 2, 3, 1>, mttkrp_kernel<FT, 2, 3, 2>}, \
-             {mttkrp_kernel<FT, 2, 4, 0>, mttkrp_kernel<FT, 2, 4, 1>, mttkrp_kernel<FT, 2, 4, 2>}}}; \
-        if (C < 1 || C > 2 || D1 < 0 || D1 > 4 || mode < 0 || mode > 2) return nullptr;  \
-        return tab[C - 1][D1][mode];                                                     \
+#define SPT_INSTANTIATE_MTTKRP_TABLE(FT, NAME)                                                                                   \
+    MttkrpKernelFn NAME(int C, int D1, int mode) {                                                                               \
+        static const MttkrpKernelFn tab[2][5][4] = {                                                                             \
+            {{mttkrp_kernel<FT, 1, 0, 0>, mttkrp_kernel<FT, 1, 0, 1>, mttkrp_kernel<FT, 1, 0, 2>, mttkrp_kernel<FT, 1, 0, 3>},   \
+             {mttkrp_kernel<FT, 1, 1, 0>, mttkrp_kernel<FT, 1, 1, 1>, mttkrp_kernel<FT, 1, 1, 2>, mttkrp_kernel<FT, 1, 1, 3>},   \
+             {mttkrp_kernel<FT, 1, 2, 0>, mttkrp_kernel<FT, 1, 2, 1>, mttkrp_kernel<FT, 1, 2, 2>, mttkrp_kernel<FT, 1, 2, 3>},   \
+             {mttkrp_kernel<FT, 1, 3, 0>, mttkrp_kernel<FT, 1, 3, 1>, mttkrp_kernel<FT, 1, 3, 2>, mttkrp_kernel<FT, 1, 3, 3>},   \
+             {mttkrp_kernel<FT, 1, 4, 0>, mttkrp_kernel<FT, 1, 4, 1>, mttkrp_kernel<FT, 1, 4, 2>, mttkrp_kernel<FT, 1, 4, 3>}},  \
+            {{mttkrp_kernel<FT, 2, 0, 0>, mttkrp_kernel<FT, 2, 0, 1>, mttkrp_kernel<FT, 2, 0, 2>, mttkrp_kernel<FT, 2, 0, 3>},   \
+             {mttkrp_kernel<FT, 2, 1, 0>, mttkrp_kernel<FT, 2, 1, 1>, mttkrp_kernel<FT, 2, 1, 2>, mttkrp_kernel<FT, 2, 1, 3>},   \
+             {mttkrp_kernel<FT, 2, 2, 0>, mttkrp_kernel<FT, 2, 2, 1>, mttkrp_kernel<FT, 2, 2, 2>, mttkrp_kernel<FT, 2, 2, 3>},   \
+             {mttkrp_kernel<FT, 2, 3, 0>, mttkrp_kernel<FT, 2, 3, 1>, mttkrp_kernel<FT, 2, 3, 2>, mttkrp_kernel<FT, 2, 3, 3>},   \
+             {mttkrp_kernel<FT, 2, 4, 0>, mttkrp_kernel<FT, 2, 4, 1>, mttkrp_kernel<FT, 2, 4, 2>, mttkrp_kernel<FT, 2, 4, 3>}}}; \
+        if (C < 1 || C > 2 || D1 < 0 || D1 > 4 || mode < 0 || mode > 3) return nullptr;                                          \
+        return tab[C - 1][D1][mode];                                                                                             \
     }
 
 }  // namespace spt

@@ -1,5 +1,7 @@
 // probe.cu -- STREAM-style copy (the bandwidth denominator the paper takes
-// from STREAM, Sec. 6) and fp32 -> 16-bit factor storage conversion.
+// from STREAM, Sec. 7), an FMA-rate probe (the arithmetic denominator of the
+// fp64 path, which is bound by GB300's fp64 units rather than by memory) and
+// fp32 -> 16-bit factor storage conversion.
 #include "internal.h"
 
 namespace spt {
@@ -22,6 +24,27 @@ __global__ void __launch_bounds__(512) stream_copy_kernel(const uint4 *__restric
         __stcs(dst + i + 3 * stride, d);
     }
     for (; i < n16; i += stride) __stcs(dst + i, __ldcs(src + i));
+}
+
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
+// Eight independent FMA chains per thread, `iters` steps each; the chains
+// converge to c / (1 - b) and their sum is stored only if it equals an
+// impossible value, which keeps them live.
+template <typename T>
+__global__ void __launch_bounds__(256) fma_probe_kernel(int64_t iters, T b, T c, double *sink) {
+    T a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (T)(threadIdx.x & 7) + (T)k;
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma_t(a[k], b, c);
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == (T)-1) *sink = (double)s;
 }
 
 __global__ void convert_bf16_kernel(const float *src, __nv_bfloat16 *dst, int64_t n) {
@@ -57,6 +80,20 @@ spt_status spt_stream_copy(const void *src, void *dst, size_t bytes, void *strea
     const int blocks = sm_count() * 4;
     stream_copy_kernel<<<blocks, 512, 0, (cudaStream_t)stream>>>((const uint4 *)src, (uint4 *)dst, n16);
     SPT_LAUNCH_CHECK("stream_copy_kernel");
+    return SPT_OK;
+}
+
+spt_status spt_fma_probe(spt_dtype dt, int64_t iters, double *sink, double *flops, void *stream) {
+    if (!sink || !flops || iters < 1) return fail(SPT_EINVAL, "spt_fma_probe: bad argument");
+    if (dt != SPT_F32 && dt != SPT_F64) return fail(SPT_EINVAL, "spt_fma_probe: dtype must be SPT_F32 or SPT_F64");
+    const int blocks = sm_count() * 8, threads = 256;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dt == SPT_F64)
+        fma_probe_kernel<double><<<blocks, threads, 0, st>>>(iters, 0.999, 0.001, sink);
+    else
+        fma_probe_kernel<float><<<blocks, threads, 0, st>>>(iters, 0.999f, 0.001f, sink);
+    SPT_LAUNCH_CHECK("fma_probe_kernel");
+    *flops = 2.0 * 8.0 * (double)iters * (double)blocks * threads;
     return SPT_OK;
 }
 

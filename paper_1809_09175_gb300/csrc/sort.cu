@@ -1,4 +1,4 @@
-// sort.cu -- mode permutations (Sec. 5), duplicate coalescing (Sec. 2 COO)
+// sort.cu -- mode permutations (Sec. 6), duplicate coalescing (Sec. 3 COO)
 // and per-mode slice statistics, built on an on-device stable LSD radix sort.
 //
 // The paper builds its permutations with library sorts (Thrust, Kokkos); this

@@ -2,7 +2,7 @@
 // exhaustive autotuner (which also produces the timing data the learned
 // selector is trained on), per-mode features, and selection by a trained
 // network.  None of this is in the paper, whose schedule is the fixed rule of
-// Tab. "sizes" (Sec. 4); that rule is kept (mttkrp_paper_schedule) as the
+// Tab. "sizes" (Sec. 5); that rule is kept (mttkrp_paper_schedule) as the
 // baseline the learned selector is measured against.
 #include <cmath>
 #include <vector>
@@ -12,8 +12,9 @@
 
 namespace spt {
 
-// candidate q = ((scatter_i * 2 + lanes_i) * 3 + npw_i) * 2 + warps_i
-static const int kScatters[3] = {SPT_SCATTER_SORTED, SPT_SCATTER_ATOMIC, SPT_SCATTER_PERM};
+// candidate q = ((scatter_i * 2 + lanes_i) * 3 + npw_i) * 2 + warps_i, scatter_i in 0..3
+static const int kScatters[4] = {SPT_SCATTER_SORTED, SPT_SCATTER_ATOMIC, SPT_SCATTER_PERM,
+                                 SPT_SCATTER_PRIVATE};
 static const int kNpw[3] = {96, 192, 384};
 static const int kWarps[2] = {4, 8};
 
@@ -39,27 +40,16 @@ spt_schedule candidate(int q, int rank) {
     return s;
 }
 
-// shared-memory bytes of a schedule (same formula as the launch)
-static size_t sched_smem(spt_tensor t, const spt_schedule &s) {
-    const int G = 32 / s.lanes_per_nnz;
-    int S = std::max(1, s.nnz_per_group);
-    if (G >= 4) S = (S & 1) ? S : S - 1;
-    else if (G == 2) S = std::max(2, (S & ~3) | 2);
-    else S = std::max(4, (S + 3) & ~3);
-    const int npw = G * S;
-    const int wpe = s.scatter == SPT_SCATTER_PERM ? 1
-                    : (s.scatter == SPT_SCATTER_SORTED ? record_words(t->d) : t->d + 1);
-    return 16 * (size_t)s.warps_per_cta + (size_t)s.warps_per_cta * carry_bytes(s.chunks, s.lanes_per_nnz) +
-           (size_t)s.warps_per_cta * 2 * wpe * npw * 4;
-}
-
-bool candidate_valid(spt_tensor t, int mode, int rank, const spt_schedule &s, int q) {
+bool candidate_valid(spt_tensor t, int mode, int rank, spt_dtype fdt, const spt_schedule &s, int q) {
     const int li = (q / 6) % 2;
     const int need = (rank + 3) / 4;
     if (li == 1 && need <= 1) return false;  // nothing to halve
     if (s.scatter == SPT_SCATTER_SORTED && !t->sorted_buf[mode]) return false;
     if (s.scatter == SPT_SCATTER_PERM && !t->perm[mode]) return false;
-    if (sched_smem(t, s) > 227 * 1024) return false;
+    const size_t smem = schedule_warp_smem(t, s, fdt);
+    if (smem > 227 * 1024) return false;
+    if (s.scatter == SPT_SCATTER_PRIVATE && private_cluster_log2(t->dims[mode], rank, smem, acc_bytes(fdt)) < 0)
+        return false;
     return true;
 }
 
@@ -74,13 +64,13 @@ spt_status mttkrp_candidates(spt_tensor t, int mode, int rank, spt_schedule *out
     if (mode < 0 || mode >= t->d || rank < 1) return fail(SPT_EINVAL, "mttkrp_candidates: bad mode/rank");
     for (int q = 0; q < SPT_NUM_CANDIDATES; ++q) {
         out[q] = candidate(q, rank);
-        if (valid) valid[q] = candidate_valid(t, mode, rank, out[q], q) ? 1 : 0;
+        if (valid) valid[q] = candidate_valid(t, mode, rank, SPT_F32, out[q], q) ? 1 : 0;
     }
     return SPT_OK;
 }
 
 spt_status mttkrp_time_schedule(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt,
-                                int rank, int ld, float *out, const spt_schedule *sched, int reps,
+                                int rank, int ld, void *out, const spt_schedule *sched, int reps,
                                 float *ms, void *stream) {
     if (!t || !sched || !ms) return fail(SPT_EINVAL, "mttkrp_time_schedule: NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
@@ -108,7 +98,7 @@ spt_status mttkrp_time_schedule(spt_tensor t, int mode, const void *const *facto
 }
 
 spt_status mttkrp_autotune(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt, int rank,
-                           int ld, float *out, int reps, spt_schedule *best, float *best_ms,
+                           int ld, void *out, int reps, spt_schedule *best, float *best_ms,
                            float *times, void *stream) {
     if (!t || !best) return fail(SPT_EINVAL, "mttkrp_autotune: NULL argument");
     if (mode < 0 || mode >= t->d || rank < 1) return fail(SPT_EINVAL, "mttkrp_autotune: bad mode/rank");
@@ -117,7 +107,7 @@ spt_status mttkrp_autotune(spt_tensor t, int mode, const void *const *factors, s
     for (int q = 0; q < SPT_NUM_CANDIDATES; ++q) {
         const spt_schedule c = candidate(q, rank);
         float ms = -1.f;
-        if (candidate_valid(t, mode, rank, c, q)) {
+        if (candidate_valid(t, mode, rank, fdt, c, q)) {
             spt_status s = mttkrp_time_schedule(t, mode, factors, fdt, rank, ld, out, &c, reps, &ms, stream);
             if (s) return s;
             if (ms < bms) { bms = ms; bq = q; }
@@ -140,7 +130,7 @@ spt_status tensor_mode_features(spt_tensor t, int mode, int rank, spt_dtype fdt,
     double other_rows = 0.0;
     for (int m = 0; m < t->d; ++m)
         if (m != mode) other_rows += (double)t->dims[m];
-    const double eb = (fdt == SPT_F32) ? 4.0 : 2.0;
+    const double eb = (double)elem_bytes(fdt);
     const double ne = std::max<double>(1.0, (double)ms.nonempty);
     const double mean_ne = P / ne;
     const double mean_all = P / In;

@@ -1,7 +1,7 @@
 """Learned MTTKRP schedule selector (not in the paper).
 
 The paper fixes its launch shape by a rule of the rank (Tab. "sizes",
-Sec. 4).  Here the exhaustive autotuner (``mttkrp_autotune``) times every
+Sec. 5).  Here the exhaustive autotuner (``mttkrp_autotune``) times every
 candidate schedule of a (tensor, mode, rank, dtype); those timings train a
 small network (``mlp_*`` kernels: forward, back-propagation, Adam, all in
 ``libspt.so``) that maps the mode's features (``tensor_mode_features``) to
@@ -170,8 +170,12 @@ class Net:
     @staticmethod
     def load(path: str) -> "Net":
         z = np.load(path)
-        return Net(torch.from_numpy(z["params"]).cuda(), z["mean"], z["std"], int(z["h1"]),
-                   int(z["h2"]))
+        h1, h2 = int(z["h1"]), int(z["h2"])
+        want = B.mlp_param_count(F, h1, h2, K)
+        if z["params"].size != want or z["mean"].size != F or z["std"].size != F:
+            raise ValueError(f"{path}: a network for {z['params'].size} parameters, this library's "
+                             f"candidate list needs {want} ({K} outputs); retrain it")
+        return Net(torch.from_numpy(z["params"]).cuda(), z["mean"], z["std"], h1, h2)
 
 
 def fit_scaling(X: np.ndarray):

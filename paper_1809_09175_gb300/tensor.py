@@ -13,7 +13,7 @@ import torch
 
 from . import binding as B
 
-_TORCH_DT = {torch.float32: "f32", torch.bfloat16: "bf16", torch.float16: "f16"}
+_TORCH_DT = {torch.float32: "f32", torch.bfloat16: "bf16", torch.float16: "f16", torch.float64: "f64"}
 
 
 def factor_ld(R: int) -> int:
@@ -96,12 +96,26 @@ class SparseTensor:
             if self.order > 1 else None
         ld = f0.shape[1] if f0 is not None else factor_ld(rank)
         fdt = _TORCH_DT[f0.dtype] if f0 is not None else "f32"
-        if out is None:
-            out = torch.empty((self.dims[mode], ld), dtype=torch.float32, device="cuda")
+        if out is None:  # float64 output for fp64 factors, float32 otherwise
+            out = torch.empty((self.dims[mode], ld), device="cuda",
+                              dtype=torch.float64 if fdt == "f64" else torch.float32)
         ptrs = [0 if (m == mode or f is None) else f.data_ptr() for m, f in enumerate(factors)]
         B.mttkrp(self.handle, mode, ptrs, fdt, rank, ld,
                  lam.data_ptr() if lam is not None else 0, out.data_ptr(), sched, _stream())
         return out
+
+    def gcp_gradient(self, mode: int, factors: List[torch.Tensor], rank: int, loss: str,
+                     out: Optional[torch.Tensor] = None):
+        """Generalised CP loss gradient with respect to factors[mode] (all d
+        factors are read); returns (grad, F) with F a 1-element float64 tensor."""
+        ld = factors[0].shape[1]
+        fdt = _TORCH_DT[factors[0].dtype]
+        if out is None:
+            out = torch.empty((self.dims[mode], ld), dtype=torch.float32, device="cuda")
+        F = torch.zeros(1, dtype=torch.float64, device="cuda")
+        B.gcp_gradient(self.handle, mode, [f.data_ptr() for f in factors], fdt, rank, ld, loss,
+                       out.data_ptr(), F.data_ptr(), _stream())
+        return out, F
 
     def cp_als_workspace(self, rank: int, ld: int) -> torch.Tensor:
         nbytes = B.cp_als_workspace_size(self.handle, rank, ld)

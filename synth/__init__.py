@@ -144,13 +144,27 @@ def factor_matrices(dims: Sequence[int], R: int, seed: int, dist: str = "uniform
 
     ``dist``: ``"uniform"`` (U(0,1)) or ``"normal"`` (N(0,1)).
     ``dtype``: ``"f32"`` -> float32 arrays; ``"bf16"`` / ``"f16"`` -> uint16
-    bit patterns of the fp32 draw rounded to nearest even.
+    bit patterns of the fp32 draw rounded to nearest even; ``"f64"`` ->
+    float64 arrays of a float64 draw.
     """
     ld = padded_ld(R) if ld is None else ld
     assert ld >= R
     g = _gens(seed + 1_000_003, len(dims))
     out = []
     for m, I in enumerate(dims):
+        if dtype == "f64":
+            if dist == "uniform":
+                a = g[m].random((int(I), R))
+            elif dist == "normal":
+                a = g[m].standard_normal((int(I), R))
+            elif dist == "int":
+                a = g[m].integers(-3, 4, size=(int(I), R)).astype(np.float64)
+            else:
+                raise ValueError(dist)
+            full = np.zeros((int(I), ld))
+            full[:, :R] = a
+            out.append(full)
+            continue
         if dist == "uniform":
             a = g[m].random((int(I), R), dtype=np.float32)
         elif dist == "normal":
@@ -222,6 +236,11 @@ WORKLOADS = {
     "zipf4d_2e6x1e5x1e4x1e3_nnz2e8": Workload(
         "zipf4d_2e6x1e5x1e4x1e3_nnz2e8", [2_000_000, 100_000, 10_000, 1_000],
         200_000_000, [1.0, 1.2, 0.8, 0.5], 64, "uniform", 0),
+    # the paper's own synthetic tensor (Sec. 7): 30K x 40K x 50K, 1e7 nonzeros at
+    # uniformly random coordinates, U(0,1) values and factors; R swept 8..256
+    "uniform3d_30kx40kx50k_nnz1e7": Workload(
+        "uniform3d_30kx40kx50k_nnz1e7", [30_000, 40_000, 50_000], 10_000_000, 0.0, 128,
+        "uniform", 0),
     # 5e5 x 2e5 x 5e4 x 5e3 x 5e2, 3e8 nonzeros, Zipf(1.1), R=32 bf16
     "zipf5d_5e5x2e5x5e4x5e3x5e2_nnz3e8": Workload(
         "zipf5d_5e5x2e5x5e4x5e3x5e2_nnz3e8", [500_000, 200_000, 50_000, 5_000, 500],

@@ -6,12 +6,12 @@ import torch
 import oracle
 import synth
 
-TORCH_DT = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+TORCH_DT = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16, "f64": torch.float64}
 
 
 def to_device_factor(f, dtype):
-    """synth factor (float32 array or uint16 bit pattern) -> CUDA tensor."""
-    if dtype == "f32":
+    """synth factor (float32 / float64 array or uint16 bit pattern) -> CUDA tensor."""
+    if dtype in ("f32", "f64"):
         return torch.from_numpy(np.ascontiguousarray(f)).cuda()
     t = torch.from_numpy(np.ascontiguousarray(f).view(np.int16)).cuda()
     return t.view(TORCH_DT[dtype])
@@ -32,7 +32,7 @@ def rel_fro(got, ref):
 # Tolerances (relative Frobenius error vs the FP64 oracle fed the same stored
 # factor values).  fp32 accumulation of products of exactly representable
 # inputs: ~ sqrt(terms per row) * 2^-24 per element; 1e-5 is the stated bound.
-TOL = {"f32": 1e-5, "bf16": 2e-3, "f16": 2e-3}
+TOL = {"f32": 1e-5, "bf16": 2e-3, "f16": 2e-3, "f64": 1e-12}
 
 
 def elementwise_bound(got, ref, scale):

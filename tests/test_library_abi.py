@@ -50,7 +50,7 @@ def test_argument_errors_without_device():
 
 
 def test_paper_sizes_table_matches_golden():
-    """Tab. "sizes" (Sec. 4) as printed: vector_size and FBS for each R range."""
+    """Tab. "sizes" (Sec. 5) as printed: vector_size and FBS for each R range."""
     import paper_1809_09175_gb300 as P
     rows = []
     for line in open(os.path.join(ROOT, "tests", "golden", "paper_tab_sizes.txt")):

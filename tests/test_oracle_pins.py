@@ -309,3 +309,70 @@ def test_mlp_gradient_matches_finite_differences():
             flat[q] = old
             fd = (lp - lm) / (2 * h)
             assert abs(fd - gflat[q]) <= 1e-6 * max(1.0, abs(fd)), (pi, q, fd, gflat[q])
+
+
+# ---- generalised CP gradient: pinned by the dense loss and its finite differences
+
+def _dense_model(factors):
+    d = len(factors)
+    letters = "abcdefg"[:d]
+    return np.einsum(",".join(f"{c}r" for c in letters) + "->" + letters, *factors)
+
+
+def _gcp_loss_dense(idx, vals, dims, factors, loss):
+    """F from the dense model tensor M: Poisson over every entry of the dense
+    tensor (duplicates summed), the other losses over the stored list."""
+    M = _dense_model(factors)
+    if loss == "poisson":
+        X = _dense(idx, vals, dims)
+        return float(M.sum() - (X[X > 0] * np.log(M[X > 0])).sum())
+    m = M[tuple(idx.astype(np.int64))]
+    x = vals.astype(np.float64)
+    if loss == "bernoulli":
+        return float((np.logaddexp(0.0, m) - x * m).sum())
+    return float(((m - x) ** 2).sum())
+
+
+@pytest.mark.parametrize("loss", ["poisson", "bernoulli", "gaussian"])
+@pytest.mark.parametrize("d", [3, 4])
+def test_gcp_gradient_is_the_derivative_of_the_dense_loss(loss, d):
+    dims = (5, 4, 3, 3)[:d]
+    R = 3
+    idx, vals = synth.coo_zipf(dims, 40, 0.7, 3 + d)  # duplicates included
+    if loss == "bernoulli":
+        vals = (vals > 0.5).astype(np.float32)
+    rng = np.random.default_rng(d)
+    A = [rng.random((I, R)) + 0.2 for I in dims]
+    for n in range(d):
+        G, F = oracle.gcp_grad(idx, vals, dims, A, n, R, loss)
+        assert abs(F - _gcp_loss_dense(idx, vals, dims, A, loss)) <= 1e-10 * max(1.0, abs(F))
+        h = 1e-6
+        fd = np.zeros_like(G)
+        for k in range(dims[n]):
+            for j in range(R):
+                Ap = [a.copy() for a in A]
+                Am = [a.copy() for a in A]
+                Ap[n][k, j] += h
+                Am[n][k, j] -= h
+                fd[k, j] = (_gcp_loss_dense(idx, vals, dims, Ap, loss) -
+                            _gcp_loss_dense(idx, vals, dims, Am, loss)) / (2 * h)
+        assert np.abs(G - fd).max() <= 1e-6 * max(1.0, np.abs(fd).max()), (loss, n)
+
+
+def test_gcp_gaussian_on_a_full_tensor_is_the_normal_equation_residual():
+    """With every coordinate stored once, the Gaussian gradient is
+    2 (A^(n) *_{l != n} A^(l)T A^(l) - MTTKRP_n(X)): the CP-ALS normal equation."""
+    dims = (4, 3, 5)
+    R = 2
+    idx = np.array(list(itertools.product(*[range(I) for I in dims]))).T.astype(np.int32)
+    vals = np.random.default_rng(0).random(idx.shape[1]).astype(np.float32)
+    rng = np.random.default_rng(1)
+    A = [rng.standard_normal((I, R)) for I in dims]
+    for n in range(3):
+        G, _ = oracle.gcp_grad(idx, vals, dims, A, n, R, "gaussian")
+        H = np.ones((R, R))
+        for l in range(3):
+            if l != n:
+                H *= A[l].T @ A[l]
+        V = oracle.mttkrp(idx, vals, dims, A, n, R)
+        np.testing.assert_allclose(G, 2 * (A[n] @ H - V), rtol=1e-10, atol=1e-10)
