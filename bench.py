@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--workload", default="zipf3d_1e6x5e5x2e5_nnz1e8")
     ap.add_argument("--dtype", default=None, help="factor storage (default: the workload's)")
     ap.add_argument("--scatter", default="sorted", choices=["atomic", "perm", "sorted", "private"])
+    ap.add_argument("--sched", default="default", choices=["default", "tuned"],
+                    help="per-mode schedule: the library's default rule or its exhaustive autotuner")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (debug only)")
     ap.add_argument("--cpu-sample", type=int, default=4_000_000,
                     help="nonzeros of the oracle's bounded CPU sample")
@@ -281,6 +283,14 @@ def run_ours(args):
         return s
 
     scheds = [sched_for(n, args.scatter, dtype) for n in range(d)]
+    tune_s = None
+    if args.sched == "tuned":  # the library's exhaustive autotuner, before the timed region
+        t0 = time.perf_counter()
+        for n in range(d):
+            best, _, _ = P.mttkrp_autotune(T.handle, n, [f.data_ptr() for f in facs], dtype, R,
+                                           ld, outs[n].data_ptr(), 2, sid)
+            scheds[n] = best
+        tune_s = time.perf_counter() - t0
     # one event pair per launch of the timed region (steps x modes)
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(d)] for _ in range(args.steps)]
@@ -368,10 +378,13 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": w.name, "dims": w.dims, "nnz": w.nnz, "zipf_s": w.s, "R": R,
                    "factors": dtype, "factor_dist": w.factor_dist, "scatter": args.scatter,
+                   "schedule": args.sched if args.sched == "default" else
+                   "exhaustive autotune per mode (untimed set-up, %.1f s)" % tune_s,
                    "step": "MTTKRP of every mode (one launch per mode)",
                    "l2": "inputs larger than L2 (COO stream "
                    f"{w.nnz * 4 * (d + 1) / 1e9:.1f} GB per mode pass)"},
         "per_mode_ms": mode_ms,
+        "schedules": [s_.as_dict() for s_ in scheds],
         "per_mode_nnzR_per_s": [w.nnz * R / (m / 1e3) for m in mode_ms],
         "roofline": {"bound": "hbm", "kernel": "mttkrp_kernel", "achieved": achieved,
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
@@ -442,6 +455,29 @@ def measure_extras(args, P, torch, w, T, idx, vals, facs_np, dtype, R, d, ld, ou
                                   "rel_err_sampled_rows": errs or None}
         del fd
     out["variants"] = var
+    # ---- generalised CP gradient (one fused launch per mode + the Poisson
+    # dense term), beside the plain MTTKRP of the same schedule
+    if args.scatter != "perm" and d >= 2:
+        fnp = w.factors(R, dtype)
+        fd = [_dev_factor(torch, f, dtype) for f in fnp]
+        if w.factor_dist == "normal":  # keep the model positive for the Poisson loss
+            fd = [f.abs() + 0.01 * (torch.arange(f.shape[1], device="cuda") < R).to(f.dtype) for f in fd]
+        gcp = {}
+        for loss in ["poisson", "bernoulli", "gaussian"]:
+            ms = []
+            for n in range(d):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                T.gcp_gradient(n, fd, R, loss, out=outs[n])
+                e0.record(stream)
+                for _ in range(3):
+                    T.gcp_gradient(n, fd, R, loss, out=outs[n])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1) / 3)
+            gcp[loss] = {"ms_per_mode": ms, "nnzR_per_s": w.nnz * R * d / (sum(ms) / 1e3)}
+        out["gcp_gradient"] = gcp
+        del fd
     # ---- CP-ALS iterations on the coalesced tensor (duplicates summed)
     Tc = P.SparseTensor(idx, vals, w.dims, coalesce=True)
     t0 = time.perf_counter()
@@ -541,7 +577,7 @@ def run_cpals(args):
             ver.append(net.choose_verified(T, n, R, fdt, facs, out, k=3))
             del out
         t_verify = time.perf_counter() - t0
-        scheds["selector_top3_verified"] = [v[0] for v in ver]
+        scheds["selector_verified"] = [v[0] for v in ver]
         sel_info = {"rank_of_exhaustive_best_in_network_order": ranks,
                     "selector_mttkrp_ms_per_mode": sel_mode_ms,
                     "verified_mttkrp_ms_per_mode": [v[1] for v in ver],
@@ -581,7 +617,7 @@ def run_cpals(args):
             "select_s": t_select, "autotune_best_ms_per_mode": auto_ms, "selector_detail": sel_info,
             "cp_als": res,
             "schedules": {k: [s_.as_dict() for s_ in v] for k, v in scheds.items()}}
-    for k in ("selector", "selector_top3_verified"):
+    for k in ("selector", "selector_verified"):
         if k in res:
             line[k + "_vs_exhaustive_time_ratio"] = res[k]["ms_per_iter"] / res["exhaustive"]["ms_per_iter"]
     print(json.dumps(line), flush=True)

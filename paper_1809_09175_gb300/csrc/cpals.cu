@@ -43,48 +43,82 @@ template <> __device__ __forceinline__ __nv_bfloat16 st_elem<__nv_bfloat16>(floa
 }
 template <> __device__ __forceinline__ __half st_elem<__half>(float v) { return __float2half_rn(v); }
 
-// Four consecutive elements as floats (p 16-byte aligned for float, 8-byte
-// for the 16-bit types).
-template <typename FT> __device__ __forceinline__ float4 ld_quad(const FT *p);
-template <> __device__ __forceinline__ float4 ld_quad<float>(const float *p) {
+// 16-byte asynchronous copy global -> shared (cp.async, L1-allocating);
+// src_bytes = 0 writes zeros without reading src.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Four consecutive stored elements widened to float.
+template <typename FT> __device__ __forceinline__ float4 quad_f(const FT *p);
+template <> __device__ __forceinline__ float4 quad_f<float>(const float *p) {
     return *reinterpret_cast<const float4 *>(p);
 }
-template <> __device__ __forceinline__ float4 ld_quad<__nv_bfloat16>(const __nv_bfloat16 *p) {
+template <> __device__ __forceinline__ float4 quad_f<__nv_bfloat16>(const __nv_bfloat16 *p) {
     const uint2 u = *reinterpret_cast<const uint2 *>(p);
     return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
                        __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
 }
-template <> __device__ __forceinline__ float4 ld_quad<__half>(const __half *p) {
+template <> __device__ __forceinline__ float4 quad_f<__half>(const __half *p) {
     const uint2 u = *reinterpret_cast<const uint2 *>(p);
     const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
     const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
-// Rows of one Gram tile per thread between barriers.
-constexpr int GRAM_ROWS_PER_THREAD = 16;
+// Shape of the Gram kernel for rank R and element size es: threads, rows of
+// a tile per team (at most 16), tile rows, shared-memory row stride
+// (elements) and bytes.
+struct GramShape {
+    int threads, rows_per_team, tile_rows, stride;
+    size_t smem;
+};
+__host__ __device__ inline GramShape gram_shape(int R, int es) {
+    const int RT = (R + 3) / 4, RP = 4 * RT, team = RT * RT;
+    const int qb = 16 / es;  // elements per 16-byte piece
+    GramShape g;
+    g.threads = team >= 256 ? team : (256 / team) * team;
+    const int RS = g.threads / team;
+    g.stride = (RP + qb - 1) / qb * qb + qb;
+    int rpt = 16;
+    while (rpt > 1 && (size_t)2 * RS * rpt * g.stride * es > 48 * 1024) --rpt;
+    g.rows_per_team = rpt;
+    g.tile_rows = RS * rpt;
+    g.smem = (size_t)2 * g.tile_rows * g.stride * es + sizeof(double) * (size_t)RP * RP;
+    return g;
+}
 
 // G += A^T A over all I rows (A row-major, stride ld, first R columns).
 // Thread (ti, tj) of a team owns the 4 x 4 block G[4ti.., 4tj..] in
-// registers; the RS teams of a CTA split the rows of each staged tile of
-// TR = 16 RS rows (quad loads, columns >= R zeroed), so every thread does 16
-// rows of FMAs per tile.  FP32 partial sums over at most 256 rows are folded
-// into the CTA's FP64 copy of G in shared memory, which each CTA adds to G
-// atomically.
+// registers; the RS teams of a CTA split the rows of each tile.  Tiles of
+// raw stored rows are double buffered with cp.async, so the next tile loads
+// while this one is multiplied.  Entries of G outside R x R (from padding
+// columns, whatever they hold) are dropped at the end.  FP32 partial sums
+// over at most 256 rows are folded into the CTA's FP64 copy of G in shared
+// memory, which each CTA adds to G atomically.
 template <typename FT>
 __global__ void __launch_bounds__(1024) gram_kernel(const FT *A, int64_t I, int ld, int R, double *G) {
     extern __shared__ __align__(16) unsigned char gsm[];
-    const int RT = (R + 3) / 4, RP = RT * 4, SP = RP + 4;
+    const GramShape sh = gram_shape(R, (int)sizeof(FT));
+    const int RT = (R + 3) / 4, RP = RT * 4;
     const int team_sz = RT * RT;
     const int RS = blockDim.x / team_sz;
-    const int TR = GRAM_ROWS_PER_THREAD * RS;
-    float *s = reinterpret_cast<float *>(gsm);                                  // TR x SP
-    double *red = reinterpret_cast<double *>(gsm + sizeof(float) * TR * SP);   // RP x RP
+    const int TR = sh.tile_rows, SPE = sh.stride;
+    constexpr int QB = 16 / (int)sizeof(FT);
+    const int PR = (RP + QB - 1) / QB;  // 16-byte pieces per row (within ld)
+    FT *const tile0 = reinterpret_cast<FT *>(gsm);  // two tiles of TR x SPE
+    const size_t tsz = (size_t)TR * SPE;
+    double *red = reinterpret_cast<double *>(gsm + (size_t)2 * TR * SPE * sizeof(FT));
     const int team = threadIdx.x / team_sz, tid = threadIdx.x % team_sz;
     const int ti = tid / RT, tj = tid % RT;
     const int RR = RP * RP;
     for (int e = threadIdx.x; e < RR; e += blockDim.x) red[e] = 0.0;
-    __syncthreads();
     float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -104,28 +138,31 @@ __global__ void __launch_bounds__(1024) gram_kernel(const FT *A, int64_t I, int 
                 }
         }
     };
-    int since = 0;
-    for (int64_t r0 = (int64_t)blockIdx.x * TR; r0 < I; r0 += (int64_t)gridDim.x * TR) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < TR * RT; e += blockDim.x) {
-            const int r = e / RT, q = e - r * RT;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (r0 + r < I) {
-                v = ld_quad<FT>(A + (r0 + r) * ld + 4 * q);
-                const int c = 4 * q;
-                if (c >= R) v.x = 0.f;
-                if (c + 1 >= R) v.y = 0.f;
-                if (c + 2 >= R) v.z = 0.f;
-                if (c + 3 >= R) v.w = 0.f;
-            }
-            *reinterpret_cast<float4 *>(&s[r * SP + 4 * q]) = v;
+    auto issue = [&](int64_t r0, FT *buf) {
+        for (int e = threadIdx.x; e < TR * PR; e += blockDim.x) {
+            const int r = e / PR, q = e - r * PR;
+            const bool in = r0 + r < I;
+            cp_async16(buf + (size_t)r * SPE + q * QB, in ? (const void *)(A + (r0 + r) * ld + q * QB) : A,
+                       in ? 16 : 0);
         }
+        cp_async_commit();
+    };
+    const int64_t step = (int64_t)gridDim.x * TR;
+    int64_t r0 = (int64_t)blockIdx.x * TR;
+    __syncthreads();  // red zeroed before the first fold
+    if (r0 < I) issue(r0, tile0);
+    int since = 0, k = 0;
+    for (; r0 < I; r0 += step, ++k) {
+        const bool next = r0 + step < I;
+        if (next) issue(r0 + step, tile0 + ((k + 1) & 1) * tsz);
+        if (next) cp_async_wait<1>(); else cp_async_wait<0>();
         __syncthreads();
+        const FT *buf = tile0 + (k & 1) * tsz;
         if (team < RS) {
             const int rmax = (int)(I - r0 < (int64_t)TR ? I - r0 : (int64_t)TR);
             for (int r = team; r < rmax; r += RS) {
-                const float4 a = *reinterpret_cast<const float4 *>(&s[r * SP + 4 * ti]);
-                const float4 b = *reinterpret_cast<const float4 *>(&s[r * SP + 4 * tj]);
+                const float4 a = quad_f<FT>(buf + (size_t)r * SPE + 4 * ti);
+                const float4 b = quad_f<FT>(buf + (size_t)r * SPE + 4 * tj);
                 const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
@@ -133,11 +170,12 @@ __global__ void __launch_bounds__(1024) gram_kernel(const FT *A, int64_t I, int 
                     for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
             }
         }
-        since += GRAM_ROWS_PER_THREAD;
+        since += sh.rows_per_team;
         if (since >= 256) {
             fold();
             since = 0;
         }
+        __syncthreads();  // this buffer is refilled by the issue two tiles on
     }
     fold();
     __syncthreads();
@@ -187,8 +225,8 @@ __global__ void __launch_bounds__(512) chol_inv_kernel(double *G, int d, int n, 
             }
             __syncthreads();
             if (fail) break;
-            const double lkk = Hs[k * R + k];
-            for (int i = k + 1 + threadIdx.x; i < R; i += blockDim.x) Hs[i * R + k] /= lkk;
+            const double rk = 1.0 / Hs[k * R + k];  // every thread: no extra barrier
+            for (int i = k + 1 + threadIdx.x; i < R; i += blockDim.x) Hs[i * R + k] *= rk;
             __syncthreads();
             const int rem = R - k - 1;
             for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
@@ -205,13 +243,15 @@ __global__ void __launch_bounds__(512) chol_inv_kernel(double *G, int d, int n, 
         if (threadIdx.x == 0) atomicExch(status, SPT_DEV_SINGULAR);
         for (int e = threadIdx.x; e < RR; e += blockDim.x) Hinv[e] = (e / R == e % R) ? 1.f : 0.f;
     } else {
-        // W = L^-1 by forward substitution, one column per thread
+        // W = L^-1 by forward substitution, one column per thread (the
+        // reciprocals of the diagonal first, so the chains carry no division)
+        for (int c = threadIdx.x; c < R; c += blockDim.x) Wd[c] = 1.0 / Hs[c * R + c];
+        __syncthreads();
         for (int c = threadIdx.x; c < R; c += blockDim.x) {
-            Wd[c] = 1.0 / Hs[c * R + c];
             for (int i = c + 1; i < R; ++i) {
                 double sacc = Hs[i * R + c] * Wd[c];
                 for (int k = c + 1; k < i; ++k) sacc += Hs[i * R + k] * Hs[c * R + k];
-                Hs[c * R + i] = -sacc / Hs[i * R + i];  // W[i][c] stored at (c, i)
+                Hs[c * R + i] = -sacc * Wd[i];  // W[i][c] stored at (c, i)
             }
         }
         __syncthreads();
@@ -233,20 +273,22 @@ __global__ void __launch_bounds__(512) chol_inv_kernel(double *G, int d, int n, 
 }
 
 // A32 = V Hinv, column sums of squares.  Thread (rq, cq) computes the 4 x 4
-// block rows [4rq, 4rq+4) x columns [4cq, 4cq+4) of a tile of V's rows; Hinv
-// and the tile (transposed, row stride TROWS + 4 against bank conflicts) sit
-// in shared memory, so each k costs two 16-byte shared loads for 16 FMAs.
-// The tile is read with 16-byte loads; sums of squares are FP32 over a
-// thread's 4 rows of a tile, then FP64.
+// block rows [4rq, 4rq+4) x columns [4cq, 4cq+4) of a tile of V's rows.
+// Tiles of V (row stride RP + 4 floats) are double buffered with cp.async;
+// Hinv sits in shared memory; each 4-wide step of k costs eight 16-byte
+// shared loads for 64 FMAs.  V's columns >= R are zero (mttkrp writes them)
+// and are skipped.  Sums of squares are FP32 over a thread's 4 rows of a
+// tile, then FP64.
 __global__ void __launch_bounds__(256) solve_kernel(const float *V, int64_t I, int ld, int R,
                                                     const float *Hinv, float *A32, double *colsq) {
     extern __shared__ __align__(16) float shs[];
     const int CT = (R + 3) / 4, RP = CT * 4;
     const int RQ = blockDim.x / CT;          // row quads per tile
     const int TROWS = 4 * RQ;
-    const int TS = TROWS + 4;
+    const int SP = RP + 4;
     float *Hs = shs;                         // R x RP
-    float *Vt = shs + R * RP;                // R x TS (transposed tile)
+    float *const vs0 = shs + R * RP;         // two tiles of TROWS x SP
+    const size_t tsz = (size_t)TROWS * SP;
     __shared__ double csq[MAXR + 4];
     for (int e = threadIdx.x; e < R * RP; e += blockDim.x) {
         const int k = e / RP, c = e % RP;
@@ -256,32 +298,48 @@ __global__ void __launch_bounds__(256) solve_kernel(const float *V, int64_t I, i
     const int rq = threadIdx.x / CT, cq = threadIdx.x % CT;
     const bool act = rq < RQ;
     double local[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t r0 = (int64_t)blockIdx.x * TROWS; r0 < I; r0 += (int64_t)gridDim.x * TROWS) {
-        __syncthreads();
+    auto issue = [&](int64_t r0, float *buf) {
         for (int e = threadIdx.x; e < TROWS * CT; e += blockDim.x) {
             const int r = e / CT, q = e - r * CT;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (r0 + r < I) v = *reinterpret_cast<const float4 *>(V + (r0 + r) * ld + 4 * q);
-            const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (4 * q + c < R) Vt[(4 * q + c) * TS + r] = vv[c];
+            const bool in = r0 + r < I;
+            cp_async16(buf + (size_t)r * SP + 4 * q, in ? (const void *)(V + (r0 + r) * ld + 4 * q) : V,
+                       in ? 16 : 0);
         }
-        __syncthreads();
+        cp_async_commit();
+    };
+    const int64_t step = (int64_t)gridDim.x * TROWS;
+    int64_t r0 = (int64_t)blockIdx.x * TROWS;
+    if (r0 < I) issue(r0, vs0);
+    for (int k = 0; r0 < I; r0 += step, ++k) {
+        const bool next = r0 + step < I;
+        if (next) issue(r0 + step, vs0 + ((k + 1) & 1) * tsz);
+        if (next) cp_async_wait<1>(); else cp_async_wait<0>();
+        __syncthreads();  // the tile (and Hs on the first pass) is visible
+        const float *vt = vs0 + (k & 1) * tsz;
         if (act) {
             float acc[4][4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-            for (int k = 0; k < R; ++k) {
-                const float4 v = *reinterpret_cast<const float4 *>(&Vt[k * TS + 4 * rq]);
-                const float4 h = *reinterpret_cast<const float4 *>(&Hs[k * RP + 4 * cq]);
-                const float vv[4] = {v.x, v.y, v.z, v.w}, hh[4] = {h.x, h.y, h.z, h.w};
+            for (int k4 = 0; k4 < CT; ++k4) {
+                float vv[4][4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 4; ++i) {
+                    const float4 v = *reinterpret_cast<const float4 *>(&vt[(4 * rq + i) * SP + 4 * k4]);
+                    vv[i][0] = v.x; vv[i][1] = v.y; vv[i][2] = v.z; vv[i][3] = v.w;
+                }
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(vv[i], hh[j], acc[i][j]);
+                for (int kk = 0; kk < 4; ++kk) {
+                    const int kr = 4 * k4 + kk;
+                    if (kr >= R) break;
+                    const float4 h = *reinterpret_cast<const float4 *>(&Hs[kr * RP + 4 * cq]);
+                    const float hh[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(vv[i][kk], hh[j], acc[i][j]);
+                }
             }
             float sq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -297,7 +355,9 @@ __global__ void __launch_bounds__(256) solve_kernel(const float *V, int64_t I, i
 #pragma unroll
             for (int j = 0; j < 4; ++j) local[j] += (double)sq[j];
         }
+        __syncthreads();  // this buffer is refilled by the issue two tiles on
     }
+    __syncthreads();  // csq zeroed (when this CTA had no tile)
     if (act)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -446,29 +506,13 @@ size_t ws_layout(spt_tensor t, int R, int ld, Ws *w, void *base) {
     return off;
 }
 
-// Launch shape of gram_kernel for rank R: threads, tile rows, shared memory.
-struct GramShape {
-    int threads, tile_rows;
-    size_t smem;
-};
-GramShape gram_shape(int R) {
-    const int RT = (R + 3) / 4, RP = 4 * RT, team = RT * RT;
-    GramShape g;
-    g.threads = team >= 256 ? team : (256 / team) * team;
-    g.tile_rows = GRAM_ROWS_PER_THREAD * (g.threads / team);
-    g.smem = sizeof(float) * (size_t)g.tile_rows * (RP + 4) + sizeof(double) * (size_t)RP * RP;
-    return g;
-}
-
 template <typename FT>
 spt_status launch_gram(const void *A, int64_t I, int ld, int R, double *G, cudaStream_t st) {
-    const GramShape g = gram_shape(R);
-    const int threads = g.threads;
-    const size_t smem = g.smem;
+    const GramShape g = gram_shape(R, (int)sizeof(FT));
     const int64_t tiles = (I + g.tile_rows - 1) / g.tile_rows;
     const int blocks = (int)std::max<int64_t>(
-        1, std::min<int64_t>(tiles, (int64_t)sm_count() * std::max(1, 1024 / threads)));
-    gram_kernel<FT><<<blocks, threads, smem, st>>>((const FT *)A, I, ld, R, G);
+        1, std::min<int64_t>(tiles, (int64_t)sm_count() * std::max(1, 1024 / g.threads)));
+    gram_kernel<FT><<<blocks, g.threads, g.smem, st>>>((const FT *)A, I, ld, R, G);
     SPT_LAUNCH_CHECK("gram_kernel");
     return SPT_OK;
 }
@@ -490,10 +534,14 @@ spt_status ensure_cpals_attrs() {
     if (done[dev]) return SPT_OK;
     SPT_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   sizeof(double) * (MAXR * MAXR + MAXR)));
-    SPT_CUDA(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  sizeof(float) * (MAXR * (MAXR + 4) + MAXR * 260)));
+    size_t ssm = 0;
+    for (int r = 1; r <= MAXR; ++r) {
+        const int ct = (r + 3) / 4, tr = 4 * (256 / ct);
+        ssm = std::max(ssm, sizeof(float) * ((size_t)r * ct * 4 + (size_t)2 * tr * (ct * 4 + 4)));
+    }
+    SPT_CUDA(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
     size_t gsm = 0;
-    for (int r = 1; r <= MAXR; ++r) gsm = std::max(gsm, gram_shape(r).smem);
+    for (int r = 1; r <= MAXR; ++r) gsm = std::max(gsm, std::max(gram_shape(r, 4).smem, gram_shape(r, 2).smem));
     SPT_CUDA(cudaFuncSetAttribute(gram_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
     SPT_CUDA(cudaFuncSetAttribute(gram_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
     SPT_CUDA(cudaFuncSetAttribute(gram_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
@@ -526,7 +574,7 @@ spt_status enqueue_step(spt_tensor t, void *const *factors, spt_dtype fdt, int R
         SPT_LAUNCH_CHECK("chol_inv_kernel");
         const int CT = (R + 3) / 4;
         const int trows = 4 * (256 / CT);
-        const size_t solve_smem = sizeof(float) * ((size_t)R * CT * 4 + (size_t)R * (trows + 4));
+        const size_t solve_smem = sizeof(float) * ((size_t)R * CT * 4 + (size_t)2 * trows * (CT * 4 + 4));
         const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((In + trows - 1) / trows, sm_count() * 2));
         solve_kernel<<<sblocks, 256, solve_smem, st>>>(w.V, In, ld, R, w.Hinv, w.A32, w.colsq);
         SPT_LAUNCH_CHECK("solve_kernel");

@@ -157,9 +157,9 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
     using AT = typename E::Acc;
     constexpr int VEC = E::VEC;
     constexpr int DA = D1 > 0 ? D1 : 1;
-    // gathered rows per nonzero: the d-1 other factors, plus the own factor's
-    // row for the generalised CP model value (slot D1)
-    constexpr int NR = GCP ? D1 + 1 : DA;
+    // gathered rows per nonzero: the d-1 other factors (the generalised CP
+    // gradient also reads the own factor's row, once per run of equal rows)
+    constexpr int NR = DA;
     constexpr int REC = record_words(D1 + 1);
     constexpr int LOADS = NR * C;
     constexpr int U = (LOADS <= 2) ? 2 : 1;
@@ -181,6 +181,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
         int col[C], nv[C];
         AT lam[C][VEC];
         const char *fb[NR][C];  // this lane's column chunk of each factor
+        const char *fbn[C];     // ... and of the own factor (generalised CP)
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             col[c] = rb * p.rb_cols + (c * L + l) * VEC;
@@ -192,7 +193,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
 #pragma unroll
             for (int m = 0; m < D1; ++m)
                 fb[m][c] = reinterpret_cast<const char *>(p.fac[m]) + (int64_t)col[c] * sizeof(FT);
-            if (GCP) fb[NR - 1][c] = reinterpret_cast<const char *>(p.fac_n) + (int64_t)col[c] * sizeof(FT);
+            fbn[c] = GCP ? reinterpret_cast<const char *>(p.fac_n) + (int64_t)col[c] * sizeof(FT) : nullptr;
         }
 
         AT acc[C][VEC], facc[C][VEC];
@@ -278,12 +279,10 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
                 for (int c = 0; c < C; ++c)
                     rw[m][c] = nv[c] > 0 ? E::load(fb[m][c] + (int64_t)r[m] * rstride) : Raw{};
             }
-            if (GCP) {
-#pragma unroll
-                for (int c = 0; c < C; ++c)
-                    rw[NR - 1][c] = nv[c] > 0 ? E::load(fb[NR - 1][c] + (int64_t)row * rstride) : Raw{};
-            }
         };
+        Raw own[C];        // generalised CP: the own factor's row of the current run
+        int own_row = -1;
+        float lsum = 0.0f; // generalised CP: this lane's loss terms of the chunk (fp32)
         // multiply out one nonzero and fold it into the running row sum;
         // `vote`: every lane of the warp runs this step (uniform fast path)
         auto step = [&](int row, float x, const Raw (&rw)[NR][C], bool vote) {
@@ -304,12 +303,14 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) fl[c][v] *= f[v];
                     }
+                    if (row != own_row) own[c] = nv[c] > 0 ? E::load(fbn[c] + (int64_t)row * rstride) : Raw{};
                     AT an[VEC];
-                    E::widen(rw[NR - 1][c], an);
+                    E::widen(own[c], an);
 #pragma unroll
                     for (int v = 0; v < VEC; ++v)
                         if (v < nv[c]) dot = fma_acc(fl[c][v], an[v], dot);
                 }
+                own_row = row;
                 const unsigned gmask = L == 32 ? FULL : (((1u << L) - 1u) << (g * L));
                 for (int o = 1; o < L; o <<= 1) dot += __shfl_xor_sync(gmask, dot, o);
                 const float mv = (float)dot;
@@ -324,7 +325,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
                     y = 2.0f * (mv - x);
                     fv = (mv - x) * (mv - x);
                 }
-                if (l == 0) *lacc += (double)fv;
+                if (l == 0) lsum += fv;
 #pragma unroll
                 for (int c = 0; c < C; ++c)
 #pragma unroll
@@ -407,6 +408,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
             }
         }
 
+        if (GCP) *lacc += (double)lsum;
         if (MODE == M_ATOMIC || MODE == M_PRIVATE) {
             if (cur >= 0) write_row(cur, acc, true);
         } else {

@@ -147,20 +147,25 @@ class Net:
         return B.mttkrp_select(T.handle, mode, fdt, rank, self.selector(), _stream())
 
     def choose_verified(self, T, mode: int, rank: int, fdt: str, factors, out, k: int = 3,
-                        reps: int = 2):
+                        reps: int = 2, with_default: bool = True):
         """Time the network's k best-ranked valid candidates (instead of all
-        SPT_NUM_CANDIDATES) and return (schedule, ms) of the fastest."""
+        SPT_NUM_CANDIDATES), and the library's default rule unless
+        with_default is False, and return (schedule, ms) of the fastest."""
         _, pred = self.choose(T, mode, rank, fdt)
         cands, valid = B.mttkrp_candidates(T.handle, mode, rank)
-        order = [q for q in np.argsort(pred) if valid[q]][:k]
+        trial = [cands[q] for q in [q for q in np.argsort(pred) if valid[q]][:k]]
+        if with_default:
+            dflt = B.mttkrp_default_schedule(T.handle, mode, fdt, rank)
+            if all(c.as_dict() != dflt.as_dict() for c in trial):
+                trial.append(dflt)
         ld = factors[0].shape[1]
         ptrs = [f.data_ptr() for f in factors]
         best, bms = None, float("inf")
-        for q in order:
+        for c in trial:
             ms = B.mttkrp_time_schedule(T.handle, mode, ptrs, fdt, rank, ld, out.data_ptr(),
-                                        cands[q], reps, _stream())
+                                        c, reps, _stream())
             if ms < bms:
-                best, bms = cands[q], ms
+                best, bms = c, ms
         return best, bms
 
     def save(self, path: str):

@@ -11,7 +11,13 @@ forward/backward/Adam kernels, and evaluated on the held-out rest.
     python -m paper_1809_09175_gb300.train_selector --count 500 --out DIR
 
 writes DIR/selector_dataset.npz, DIR/selector_weights.npz and
-DIR/selector_report.json.
+DIR/selector_report.json;
+
+    python -m paper_1809_09175_gb300.train_selector --extend OLD/selector_dataset.npz \
+        --large 40 --nnz-hi 3e7 --large-hi 3e8 --out DIR
+
+appends 40 more training tensors with 3e7..3e8 nonzeros to a saved dataset
+and trains on the union (the held-out tensors stay the same).
 """
 from __future__ import annotations
 
@@ -107,7 +113,10 @@ def main():
     ap.add_argument("--count", type=int, default=500)
     ap.add_argument("--nnz-lo", type=float, default=1e5)
     ap.add_argument("--nnz-hi", type=float, default=1e7)
-    ap.add_argument("--large", type=int, default=0, help="extra tensors with nnz in [nnz_hi, 1.5e8]")
+    ap.add_argument("--large", type=int, default=0, help="extra tensors with nnz in [nnz_hi, large_hi]")
+    ap.add_argument("--large-hi", type=float, default=1.5e8)
+    ap.add_argument("--extend", default=None,
+                    help="append --large new training tensors (other seeds) to this saved dataset")
     ap.add_argument("--holdout", type=float, default=0.1)
     ap.add_argument("--epochs", type=int, default=4000)
     ap.add_argument("--reps", type=int, default=1)
@@ -119,11 +128,33 @@ def main():
     if a.dataset:
         z = np.load(a.dataset)
         return train_and_report(a, z["X"], z["times"], z["t_paper"], z["t_default"], z["meta"],
-                                int(z["n_train_tensors"]) if "n_train_tensors" in z else None, 0.0)
+                                int(z["n_train_tensors"]) if "n_train_tensors" in z else None, 0.0,
+                                z["train_mask"] if "train_mask" in z else None)
+    if a.extend:
+        z = np.load(a.extend)
+        meta0 = z["meta"]
+        mask0 = z["train_mask"] if "train_mask" in z else meta0[:, 0] < int(z["n_train_tensors"])
+        big = synth.selector_specs(a.large, seed0=30_000, nnz_lo=a.nnz_hi, nnz_hi=a.nnz_hi,
+                                   large=a.large, large_hi=a.large_hi)
+        X, TT, TP, TD, meta = [list(z[k]) for k in ("X", "times", "t_paper", "t_default", "meta")]
+        base = int(meta0[:, 0].max()) + 1
+        t0 = time.time()
+        for i, w in enumerate(big):
+            fdt = "bf16" if i % 2 else "f32"
+            for n, (f, t, tp, td) in enumerate(measure_tensor(w, fdt, a.reps)):
+                X.append(f); TT.append(t); TP.append(tp); TD.append(td)
+                meta.append(np.array((base + i, n, w.R, 0 if fdt == "f32" else 1, w.nnz, len(w.dims))))
+            print(f"{i + 1}/{len(big)} extra tensors, {time.time() - t0:.0f} s", flush=True)
+        X = np.array(X, np.float32); TT = np.array(TT, np.float32)
+        TP = np.array(TP, np.float32); TD = np.array(TD, np.float32); meta = np.array(meta, np.int64)
+        mask = np.concatenate([mask0, np.ones(len(meta) - len(meta0), bool)])
+        np.savez(os.path.join(a.out, "selector_dataset.npz"), X=X, times=TT, t_paper=TP, t_default=TD,
+                 meta=meta, train_mask=mask)
+        return train_and_report(a, X, TT, TP, TD, meta, None, time.time() - t0, mask)
     specs = synth.selector_specs(a.count, nnz_lo=a.nnz_lo, nnz_hi=a.nnz_hi)
     # larger tensors join the training part only (the held-out part keeps the base recipe)
     big = synth.selector_specs(a.large, seed0=20_000, nnz_lo=a.nnz_hi, nnz_hi=a.nnz_hi,
-                               large=a.large) if a.large else []
+                               large=a.large, large_hi=a.large_hi) if a.large else []
     specs = specs[: int(round(len(specs) * (1 - a.holdout)))] + big + \
         specs[int(round(len(specs) * (1 - a.holdout))):]
     X, TT, TP, TD, meta = [], [], [], [], []
@@ -143,10 +174,14 @@ def main():
     train_and_report(a, X, TT, TP, TD, meta, n_train_tensors, time.time() - t0)
 
 
-def train_and_report(a, X, TT, TP, TD, meta, n_train_tensors, dataset_s):
-    if n_train_tensors is None:  # datasets saved before the split was recorded: 450 + 30 large
-        n_train_tensors = int(meta[:, 0].max() + 1) - 50
-    tr = meta[:, 0] < n_train_tensors
+def train_and_report(a, X, TT, TP, TD, meta, n_train_tensors, dataset_s, train_mask=None):
+    if train_mask is not None:
+        tr = np.asarray(train_mask, bool)
+        n_train_tensors = int(len(np.unique(meta[tr, 0])))
+    else:
+        if n_train_tensors is None:  # datasets saved before the split was recorded: 450 + 30 large
+            n_train_tensors = int(meta[:, 0].max() + 1) - 50
+        tr = meta[:, 0] < n_train_tensors
     te = ~tr
     mean, std = S.fit_scaling(X[tr])
     net = S.Net.init(0, mean=mean, std=std)

@@ -76,3 +76,61 @@ def test_dense_pin_rejects_planted_mistake(name):
             if not np.allclose(got, ref, rtol=1e-12, atol=1e-12):
                 caught = True
         assert caught, f"planted mistake {name} passed the dense pin"
+
+
+# planted mistakes in the generalised CP gradient, caught by the dense-loss /
+# finite-difference pin of tests/test_oracle_pins.py
+GCP_MUTATIONS = {
+    "poisson_sign": ("            y = -x / m;                 /* the stored entry's part of 1 - x/m */",
+                     "            y = x / m;"),
+    "dense_term_dropped": ("            for (int64_t k = 0; k < In; ++k) G[k * ldg + j] += c;",
+                           "            (void)c;"),
+    "own_mode_in_dense_term": ("                if (l != n) c *= cs;", "                c *= cs;"),
+    "bernoulli_derivative": ("            y = 1.0 / (1.0 + exp(-m)) - x;", "            y = 1.0 / (1.0 + exp(m)) - x;"),
+    "gaussian_factor_two": ("            y = 2.0 * (m - x);", "            y = (m - x);"),
+    "own_factor_in_product": ("            for (int l = 0; l < d; ++l) {\n                if (l == n) continue;\n                t *= A[l]",
+                              "            for (int l = 0; l < d; ++l) {\n                t *= A[l]"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GCP_MUTATIONS))
+def test_gcp_pin_rejects_planted_mistake(name):
+    from tests.test_oracle_pins import _gcp_loss_dense
+    dims = (5, 4, 3)
+    R = 2
+    idx, vals = synth.coo_zipf(dims, 30, 0.7, 9)
+    rng = np.random.default_rng(2)
+    A = [rng.random((I, R)) + 0.2 for I in dims]
+    dp = C.POINTER(C.c_double)
+    fs = [np.ascontiguousarray(a) for a in A]
+    arr = (dp * 3)(*[f.ctypes.data_as(dp) for f in fs])
+    lda = np.array([R] * 3, dtype=np.int64)
+    dims_a = np.array(dims, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    caught = False
+    with tempfile.TemporaryDirectory() as tmp:
+        L = _build_variant(name, *GCP_MUTATIONS[name], tmp)
+        L.oracle_gcp_grad.argtypes = [C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int,
+                                      C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int64]
+        L.oracle_gcp_grad.restype = C.c_double
+        for loss, code in (("poisson", 0), ("bernoulli", 1), ("gaussian", 2)):
+            v = vals if loss != "bernoulli" else (vals > 0.5).astype(np.float32)
+            v64 = np.ascontiguousarray(v, dtype=np.float64)
+            for n in range(3):
+                G = np.zeros((dims[n], R))
+                F = L.oracle_gcp_grad(3, dims_a.ctypes.data, idx.shape[1], idx.ctypes.data, v64.ctypes.data,
+                                      n, R, C.cast(arr, C.c_void_p), lda.ctypes.data, code, G.ctypes.data, R)
+                Fd = _gcp_loss_dense(idx, v, dims, A, loss)
+                h = 1e-6
+                fd = np.zeros_like(G)
+                for k in range(dims[n]):
+                    for j in range(R):
+                        Ap = [a.copy() for a in A]
+                        Am = [a.copy() for a in A]
+                        Ap[n][k, j] += h
+                        Am[n][k, j] -= h
+                        fd[k, j] = (_gcp_loss_dense(idx, v, dims, Ap, loss) -
+                                    _gcp_loss_dense(idx, v, dims, Am, loss)) / (2 * h)
+                if abs(F - Fd) > 1e-10 * max(1.0, abs(Fd)) or np.abs(G - fd).max() > 1e-6 * max(1.0, np.abs(fd).max()):
+                    caught = True
+    assert caught, f"planted mistake {name} passed the generalised CP pin"
