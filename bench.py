@@ -42,8 +42,10 @@ def parse():
     ap.add_argument("--workload", default="zipf3d_1e6x5e5x2e5_nnz1e8")
     ap.add_argument("--dtype", default=None, help="factor storage (default: the workload's)")
     ap.add_argument("--scatter", default="sorted", choices=["atomic", "perm", "sorted", "private"])
-    ap.add_argument("--sched", default="default", choices=["default", "tuned"],
-                    help="per-mode schedule: the library's default rule or its exhaustive autotuner")
+    ap.add_argument("--sched", default="tuned", choices=["default", "tuned"],
+                    help="per-mode schedule: the library's exhaustive autotuner (set-up, untimed) "
+                         "or its default rule")
+    ap.add_argument("--npg", type=int, default=0, help="override the schedule's nonzeros per lane group")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (debug only)")
     ap.add_argument("--cpu-sample", type=int, default=4_000_000,
                     help="nonzeros of the oracle's bounded CPU sample")
@@ -280,6 +282,8 @@ def run_ours(args):
     def sched_for(n, scatter, fdt):
         s = P.mttkrp_default_schedule(T.handle, n, fdt, R)
         s.scatter = P.SCATTERS[scatter]
+        if args.npg:
+            s.nnz_per_group = args.npg
         return s
 
     scheds = [sched_for(n, args.scatter, dtype) for n in range(d)]

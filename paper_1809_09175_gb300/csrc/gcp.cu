@@ -121,6 +121,7 @@ spt_status gcp_gradient(spt_tensor t, int mode, const void *const *factors, spt_
         return fail(SPT_ESTATE, "gcp_gradient: needs the mode-sorted copy (build_mode_permutation)");
     spt_schedule s = default_schedule(t, mode, fdt, rank);
     s.scatter = SPT_SCATTER_SORTED;
+    s.warps_per_cta = std::min(s.warps_per_cta, 8);  // gcp_kernel's launch bound: 256 threads
     if (s.lanes_per_nnz * s.chunks * 4 < rank) {  // the default rule covers R <= 256 in one block
         s.lanes_per_nnz = 32;
         s.chunks = 2;

@@ -157,9 +157,9 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
     using AT = typename E::Acc;
     constexpr int VEC = E::VEC;
     constexpr int DA = D1 > 0 ? D1 : 1;
-    // gathered rows per nonzero: the d-1 other factors (the generalised CP
-    // gradient also reads the own factor's row, once per run of equal rows)
-    constexpr int NR = DA;
+    // gathered rows per nonzero: the d-1 other factors, plus the own factor's
+    // row for the generalised CP model value (slot D1)
+    constexpr int NR = GCP ? D1 + 1 : DA;
     constexpr int REC = record_words(D1 + 1);
     constexpr int LOADS = NR * C;
     constexpr int U = (LOADS <= 2) ? 2 : 1;
@@ -181,7 +181,6 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
         int col[C], nv[C];
         AT lam[C][VEC];
         const char *fb[NR][C];  // this lane's column chunk of each factor
-        const char *fbn[C];     // ... and of the own factor (generalised CP)
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             col[c] = rb * p.rb_cols + (c * L + l) * VEC;
@@ -193,7 +192,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
 #pragma unroll
             for (int m = 0; m < D1; ++m)
                 fb[m][c] = reinterpret_cast<const char *>(p.fac[m]) + (int64_t)col[c] * sizeof(FT);
-            fbn[c] = GCP ? reinterpret_cast<const char *>(p.fac_n) + (int64_t)col[c] * sizeof(FT) : nullptr;
+            if (GCP) fb[NR - 1][c] = reinterpret_cast<const char *>(p.fac_n) + (int64_t)col[c] * sizeof(FT);
         }
 
         AT acc[C][VEC], facc[C][VEC];
@@ -279,10 +278,13 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
                 for (int c = 0; c < C; ++c)
                     rw[m][c] = nv[c] > 0 ? E::load(fb[m][c] + (int64_t)r[m] * rstride) : Raw{};
             }
+            if (GCP) {
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    rw[NR - 1][c] = nv[c] > 0 ? E::load(fb[NR - 1][c] + (int64_t)row * rstride) : Raw{};
+            }
         };
-        Raw own[C];        // generalised CP: the own factor's row of the current run
-        int own_row = -1;
-        float lsum = 0.0f; // generalised CP: this lane's loss terms of the chunk (fp32)
+        float lsum = 0.0f;  // generalised CP: this lane's loss terms of the chunk (fp32)
         // multiply out one nonzero and fold it into the running row sum;
         // `vote`: every lane of the warp runs this step (uniform fast path)
         auto step = [&](int row, float x, const Raw (&rw)[NR][C], bool vote) {
@@ -303,24 +305,24 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) fl[c][v] *= f[v];
                     }
-                    if (row != own_row) own[c] = nv[c] > 0 ? E::load(fbn[c] + (int64_t)row * rstride) : Raw{};
                     AT an[VEC];
-                    E::widen(own[c], an);
+                    E::widen(rw[NR - 1][c], an);
 #pragma unroll
                     for (int v = 0; v < VEC; ++v)
                         if (v < nv[c]) dot = fma_acc(fl[c][v], an[v], dot);
                 }
-                own_row = row;
                 const unsigned gmask = L == 32 ? FULL : (((1u << L) - 1u) << (g * L));
                 for (int o = 1; o < L; o <<= 1) dot += __shfl_xor_sync(gmask, dot, o);
                 const float mv = (float)dot;
                 float y, fv;
+                // fast-math intrinsics: a few ulp, far inside the 2e-5 gradient bound
                 if (p.loss == 0) {  // Poisson: the stored entry's part of 1 - x/m
-                    y = -x / mv;
-                    fv = -x * logf(mv);
+                    y = -__fdividef(x, mv);
+                    fv = -x * __logf(mv);
                 } else if (p.loss == 1) {  // Bernoulli, logit link
-                    y = 1.0f / (1.0f + expf(-mv)) - x;
-                    fv = (mv > 0.0f ? mv + log1pf(expf(-mv)) : log1pf(expf(mv))) - x * mv;
+                    const float e = __expf(-fabsf(mv));  // log(1 + e^m) = max(m, 0) + log(1 + e^-|m|)
+                    y = (mv >= 0.0f ? __fdividef(1.0f, 1.0f + e) : __fdividef(e, 1.0f + e)) - x;
+                    fv = fmaxf(mv, 0.0f) + __logf(1.0f + e) - x * mv;
                 } else {  // Gaussian
                     y = 2.0f * (mv - x);
                     fv = (mv - x) * (mv - x);
@@ -681,7 +683,7 @@ __device__ __forceinline__ void mttkrp_warp_range(const MttkrpParams &p, unsigne
 // Generalised CP gradient over the mode-sorted copy: the MTTKRP traversal
 // with each nonzero's value replaced by df/dm at the model value m.
 template <typename FT, int C, int D1>
-__global__ void __launch_bounds__(512, 1) gcp_kernel(const MttkrpParams p) {
+__global__ void __launch_bounds__(256, 3) gcp_kernel(const MttkrpParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     mttkrp_warp_range<FT, C, D1, M_SORTED, true>(p, smem_raw, nullptr);
 }
