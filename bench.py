@@ -489,6 +489,12 @@ def measure_extras(args, P, torch, w, T, idx, vals, facs_np, dtype, R, d, ld, ou
     torch.cuda.synchronize()
     sort_s = time.perf_counter() - t0
     fc = [_dev_factor(torch, f, dtype) for f in facs_np]
+    tuned = args.sched == "tuned"
+    if tuned:  # the autotuner's schedule per mode, recorded on the tensor for cp_als_step
+        for n in range(d):
+            best, _, _ = P.mttkrp_autotune(Tc.handle, n, [f.data_ptr() for f in fc], dtype, R, ld,
+                                           outs[n].data_ptr(), 2, stream.cuda_stream)
+            P.tensor_set_schedule(Tc.handle, n, dtype, R, best)
     lam = torch.zeros(R, dtype=torch.float64, device="cuda")
     fit = torch.zeros(1, dtype=torch.float64, device="cuda")
     ws = Tc.cp_als_workspace(R, ld)
@@ -506,6 +512,7 @@ def measure_extras(args, P, torch, w, T, idx, vals, facs_np, dtype, R, d, ld, ou
     torch.cuda.synchronize()
     it_ms = e0.elapsed_time(e1) / iters
     out["cp_als"] = {"nnz_coalesced": Tc.nnz, "ms_per_iter": it_ms, "iter_per_s": 1e3 / it_ms,
+                     "schedules": "autotuned per mode" if tuned else "default rule",
                      "fit": float(fit.item()), "graph": True,
                      "permutation_build_s": sort_s,
                      "permutation_cost_in_iterations": sort_s * 1e3 / it_ms}

@@ -74,11 +74,14 @@ spt_schedule default_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank) {
     while (lanes < need && lanes < 32) lanes <<= 1;
     s.lanes_per_nnz = lanes;
     s.chunks = need > 32 ? 2 : 1;
-    // about 7 KB of shared memory per warp (two staging buffers plus the run
-    // carry), so four 8-warp CTAs fit an SM; at most 256 nonzeros per chunk
+    // at most 6 KB of shared memory per warp (barriers, run carry, two
+    // staging buffers): four 8-warp CTAs then fit the 196 KB shared-memory
+    // carve-out and leave ~60 KB of the SM's L1 for factor-row hits (with
+    // 7 KB the 228 KB carve-out leaves 28 KB and the 3-way 1e8 MTTKRP runs
+    // 20% slower); at most 256 nonzeros per chunk
     const int narr = s.scatter == SPT_SCATTER_PERM ? 1
                      : (s.scatter == SPT_SCATTER_SORTED ? record_words(t->d) : t->d + 1);
-    const int npw = std::min(256, (7168 - 16 - carry_bytes(s.chunks, lanes, acc_bytes(fdt))) / (8 * narr));
+    const int npw = std::min(256, (6144 - 16 - carry_bytes(s.chunks, lanes, acc_bytes(fdt))) / (8 * narr));
     s.nnz_per_group = std::max(4, npw / (32 / lanes));
     s.warps_per_cta = 8;
     s.ctas_per_sm = 0;

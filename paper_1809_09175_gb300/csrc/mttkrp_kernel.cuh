@@ -28,8 +28,9 @@
 //                the permutation is staged, coordinates and values gathered.
 //                For both, a group writes a finished row with a plain store;
 //                the first and last run of every group are combined across
-//                the warp with shuffles (a segmented reduction over the
-//                groups), and the last open run is carried in shared memory
+//                the warp with shuffles (a log-step segmented scan over the
+//                groups' tail runs, after which each group writes the runs
+//                that end in it), and the last open run is carried in shared memory
 //                into the warp's next chunk, so only the first and last row
 //                of the warp's whole range are added atomically: only those
 //                rows can be shared with other warps.
@@ -414,11 +415,88 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
         if (MODE == M_ATOMIC || MODE == M_PRIVATE) {
             if (cur >= 0) write_row(cur, acc, true);
         } else {
-            // Segmented combine of the groups' open runs, in group order.
-            // Every lane tracks the running (orow, oacc) for its columns;
-            // group 0's lanes perform the writes.
+            // Segmented combine of the groups' open runs.  Every group holds
+            // a tail run (cur, acc) and, if it saw a row change, a closed
+            // head run (frow, facc); rows between them are already written.
             int *crow_p = reinterpret_cast<int *>(carry);
             AT *cacc_p = carry ? reinterpret_cast<AT *>(carry + 16) + l * (C * VEC) : nullptr;
+            const int s0 = carry ? crow_p[1] : b0, s1 = carry ? crow_p[2] : b1;
+            auto shared_row = [&](int row) { return row == s0 || row == s1; };
+            if (n == npw && G > 1) {
+                // Full chunk (every group non-empty): a log-step segmented
+                // scan of the tails over the groups, then each group writes
+                // the runs that end in it.  A group's tail continues the
+                // previous group's chain unless it has a head or a new row.
+                const int crow = carry ? *crow_p : -1;
+                const int first = fclosed ? frow : cur;
+                int prevrow = __shfl_up_sync(FULL, cur, L);
+                if (g == 0) prevrow = crow;
+                AT cin[C][VEC], T[C][VEC];
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        cin[c][v] = carry ? cacc_p[c * VEC + v] : (AT)0;
+                        T[c][v] = acc[c][v];
+                    }
+                int f = (fclosed || cur != prevrow) ? 1 : 0;
+                if (g == 0 && !f) {  // the carried run continues into group 0's tail
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) T[c][v] += cin[c][v];
+                }
+                if (g == 0 && crow >= 0 && first != crow) write_row(crow, cin, shared_row(crow));
+                for (int off = 1; off < G; off <<= 1) {
+                    const int fu = __shfl_up_sync(FULL, f, off * L);
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            const AT tu = __shfl_up_sync(FULL, T[c][v], off * L);
+                            if (g >= off && !f) T[c][v] += tu;
+                        }
+                    if (g >= off) f |= fu;
+                }
+                // the chain ending in group g-1 (the carry for group 0)
+                AT Sp[C][VEC];
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        const AT su = __shfl_up_sync(FULL, T[c][v], L);
+                        Sp[c][v] = g == 0 ? cin[c][v] : su;
+                    }
+                const int nf = __shfl_down_sync(FULL, first, L);  // first row of group g+1
+                if (fclosed) {  // the head joins the chain ending before it if the rows agree
+                    if (frow == prevrow) {
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) facc[c][v] += Sp[c][v];
+                    }
+                    write_row(frow, facc, shared_row(frow));
+                }
+                if (g < G - 1) {
+                    if (nf != cur) write_row(cur, T, shared_row(cur));  // the chain ends here
+                } else if (!carry) {
+                    write_row(cur, T, shared_row(cur));
+                }
+                if (carry) {
+                    __syncwarp();  // every lane has read the carry
+                    if (g == G - 1) {
+                        if (l == 0) *crow_p = cur;
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) cacc_p[c * VEC + v] = T[c][v];
+                    }
+                }
+                continue;  // next rank block
+            }
+            // Ragged chunk or one group: the groups' runs in group order.
+            // Every lane tracks the running (orow, oacc) for its columns;
+            // group 0's lanes perform the writes.
             AT oacc[C][VEC];
 #pragma unroll
             for (int c = 0; c < C; ++c)
@@ -427,10 +505,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
             int orow = carry ? *crow_p : -1;
             const bool writer = (g == 0);
             auto emit = [&](int row, AT (&a)[C][VEC]) {
-                if (writer) {
-                    const int s0 = carry ? crow_p[1] : b0, s1 = carry ? crow_p[2] : b1;
-                    write_row(row, a, row == s0 || row == s1);
-                }
+                if (writer) write_row(row, a, shared_row(row));
             };
             for (int g2 = 0; g2 < G; ++g2) {
                 const int srcl = (g2 << log2L) | l;
