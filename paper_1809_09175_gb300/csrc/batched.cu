@@ -1,13 +1,15 @@
 // batched.cu -- MTTKRP of all modes of many tensors in one persistent launch.
 //
 // Every (tensor, mode) pair is a task; a task's nonzeros (its mode-sorted
-// packed records) are cut into chunks of its schedule's npw nonzeros, and all
-// chunks of all tasks form one global item space.  A persistent grid of warps
-// claims items with an atomic counter (uneven tensors balance themselves),
-// stages each item's records with a bulk copy while the previous item is
-// computed, and runs the same per-chunk routine as the single-tensor kernel
-// (Sec. 6 permuted traversal over sorted nonzeros, Fig. MTTKRP-C).  One
-// zero-fill kernel clears every output and the counter first; the two
+// packed records) are cut into chunks of its schedule's npw nonzeros, and a
+// task's chunks into blocks of BATCH_BLOCK_CHUNKS.  Tasks are grouped by
+// kernel class (chunks per lane C, order - 1): every class runs one
+// persistent kernel specialised for it, whose warps claim blocks with an
+// atomic counter (uneven tensors balance themselves) and walk each block as
+// a contiguous range with the single-tensor kernel's range routine: staged
+// bulk copies, the segmented combine and the run carried across the block's
+// chunks (Sec. 6 permuted traversal over sorted nonzeros, Fig. MTTKRP-C).
+// One zero-fill kernel clears every output and the counters first; the
 // launches are captured once in a CUDA graph and replayed.
 #include <vector>
 
@@ -17,11 +19,11 @@
 namespace spt {
 namespace {
 
+constexpr int BATCH_BLOCK_CHUNKS = 8;  // chunks a warp claims at a time
+
 struct BatchTask {
-    MttkrpParams p;      // M_SORTED parameters of this (tensor, mode)
-    int64_t first_item;  // first chunk of this task in the global item space
-    int d1;              // order - 1
-    int C;               // chunks per lane
+    MttkrpParams p;       // M_SORTED parameters of this (tensor, mode)
+    int64_t first_block;  // first block of this task in its class's block space
 };
 
 struct ZeroSeg {
@@ -29,8 +31,9 @@ struct ZeroSeg {
     int64_t n;
 };
 
-__global__ void batch_zero_kernel(const ZeroSeg *segs, int nseg, unsigned long long *counter) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0ull;
+__global__ void batch_zero_kernel(const ZeroSeg *segs, int nseg, unsigned long long *counters, int ncnt) {
+    if (blockIdx.x == 0 && blockIdx.y == 0)
+        for (int c = threadIdx.x; c < ncnt; c += blockDim.x) counters[c] = 0ull;
     for (int s = blockIdx.y; s < nseg; s += gridDim.y) {
         float4 *p4 = reinterpret_cast<float4 *>(segs[s].ptr);
         const int64_t n4 = segs[s].n / 4;  // outputs are I x ld with ld % 8 == 0
@@ -40,117 +43,71 @@ __global__ void batch_zero_kernel(const ZeroSeg *segs, int nseg, unsigned long l
     }
 }
 
-__device__ __forceinline__ int find_task(const BatchTask *tasks, int ntasks, int64_t item) {
-    int lo = 0, hi = ntasks - 1;  // last task with first_item <= item
+__device__ __forceinline__ int find_task(const BatchTask *tasks, int ntasks, int64_t blk) {
+    int lo = 0, hi = ntasks - 1;  // last task with first_block <= blk
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (tasks[mid].first_item <= item) lo = mid; else hi = mid - 1;
+        if (tasks[mid].first_block <= blk) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
 
+// Persistent kernel of one class (FT, C, D1).  Shared memory per warp: two
+// barriers (first 16 * wpc bytes), a carry slot of cb bytes, two staging
+// buffers of stage_words words each (the largest task of the class).
 template <typename FT, int C, int D1>
-__device__ __forceinline__ void run_chunk(const MttkrpParams &p, const int32_t *buf, int n) {
-    int b0, b1;
-    chunk_bounds<D1, M_SORTED>(p, buf, n, b0, b1);
-    mttkrp_chunk<FT, C, D1, M_SORTED>(p, buf, n, b0, b1, nullptr, nullptr);
-}
-
-template <typename FT>
-__device__ __forceinline__ void run_item(const MttkrpParams &p, int d1, int C, const int32_t *buf, int n) {
-    switch (d1 * 2 + C - 1) {
-    case 2: run_chunk<FT, 1, 1>(p, buf, n); break;
-    case 3: run_chunk<FT, 2, 1>(p, buf, n); break;
-    case 4: run_chunk<FT, 1, 2>(p, buf, n); break;
-    case 5: run_chunk<FT, 2, 2>(p, buf, n); break;
-    case 6: run_chunk<FT, 1, 3>(p, buf, n); break;
-    case 7: run_chunk<FT, 2, 3>(p, buf, n); break;
-    case 8: run_chunk<FT, 1, 4>(p, buf, n); break;
-    case 9: run_chunk<FT, 2, 4>(p, buf, n); break;
-    default: break;
-    }
-}
-
-template <typename FT>
-__global__ void __launch_bounds__(256, 2) mttkrp_batch_kernel(const BatchTask *__restrict__ tasks,
-                                                             int ntasks, int64_t total,
-                                                             unsigned long long *counter,
-                                                             int stage_words, int *err) {
+__global__ void __launch_bounds__(256, C == 1 ? 3 : 2)
+    mttkrp_batch_kernel(const BatchTask *__restrict__ tasks, int ntasks, int64_t total_blocks,
+                        unsigned long long *counter, int stage_words, int cb) {
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpc = blockDim.x >> 5;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw) + 2 * warp;
-    int32_t *wbuf = reinterpret_cast<int32_t *>(smem_raw + 16 * wpc) + (size_t)warp * 2 * stage_words;
-
-    if (lane == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        fence_mbar_init();
-        fence_proxy_async_smem();
-    }
-    __syncwarp();
-
-    auto claim = [&]() -> int64_t {
+    unsigned char *carry = smem_raw + 16 * wpc + (size_t)warp * cb;
+    int32_t *wbuf = reinterpret_cast<int32_t *>(smem_raw + 16 * wpc + (size_t)wpc * cb) +
+                    (size_t)warp * 2 * stage_words;
+    warp_bars_init(bars);
+    uint32_t k = 0;
+    for (;;) {
         unsigned long long it = 0;
         if (lane == 0) it = atomicAdd(counter, 1ull);
-        return (int64_t)__shfl_sync(FULL, it, 0);
-    };
-    auto item_len = [&](const BatchTask &tk, int64_t item) {
-        const int64_t c0 = (item - tk.first_item) * tk.p.npw;
-        const int64_t rem = tk.p.nnz - c0;
-        return (int)(rem < tk.p.npw ? rem : tk.p.npw);
-    };
-    auto issue = [&](int64_t item, int tix, int s) {  // lane 0
-        const BatchTask &tk = tasks[tix];
-        const int rw = record_words(tk.d1 + 1);
-        const int n = item_len(tk, item);
-        const int64_t c0 = (item - tk.first_item) * tk.p.npw;
-        const uint32_t bytes = (uint32_t)((n * rw) & ~3) * 4u;
-        mbar_arrive_expect_tx(&bars[s], bytes);
-        if (bytes) bulk_g2s(wbuf + s * stage_words, tk.p.rec + c0 * rw, bytes, &bars[s]);
-    };
-
-    int64_t nxt = claim();
-    int tix_n = nxt < total ? find_task(tasks, ntasks, nxt) : 0;
-    if (nxt < total && lane == 0) issue(nxt, tix_n, 0);
-    int k = 0;
-    while (nxt < total) {
-        const int64_t cur = nxt;
-        const int tix = tix_n;
-        nxt = claim();
-        if (nxt < total) {
-            tix_n = find_task(tasks, ntasks, nxt);
-            if (lane == 0) {
-                fence_proxy_async_smem();
-                issue(nxt, tix_n, (k + 1) & 1);
-            }
-        }
-        const int s = k & 1;
-        const uint32_t parity = (uint32_t)(k >> 1) & 1u;
-        const bool ok = mbar_wait(&bars[s], parity);
-        if (!__all_sync(FULL, ok)) {
-            if (lane == 0) atomicExch(err, SPT_DEV_TIMEOUT);
-            if (nxt < total) mbar_wait(&bars[s ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
-            mbar_wait(&bars[s], parity);
-            return;
-        }
-        const MttkrpParams p = tasks[tix].p;
-        const int d1 = tasks[tix].d1, C = tasks[tix].C;
-        const int rw = record_words(d1 + 1);
-        int32_t *buf = wbuf + s * stage_words;
-        const int n = item_len(tasks[tix], cur);
-        {  // words past the 16-byte body of a ragged chunk
-            const int64_t c0 = (cur - tasks[tix].first_item) * p.npw;
-            const int W = n * rw, wb = W & ~3;
-            if (lane < W - wb) buf[wb + lane] = __ldg(p.rec + c0 * rw + wb + lane);
-        }
-        __syncwarp();
-        run_item<FT>(p, d1, C, buf, n);
-        __syncwarp();  // the stage is free before it is refilled
-        ++k;
+        const int64_t blk = (int64_t)__shfl_sync(FULL, it, 0);
+        if (blk >= total_blocks) break;
+        const int t = find_task(tasks, ntasks, blk);
+        const MttkrpParams &p = tasks[t].p;  // read through the cache, not copied to registers
+        const int64_t c0 = (blk - tasks[t].first_block) * BATCH_BLOCK_CHUNKS;
+        const int64_t c1 = c0 + BATCH_BLOCK_CHUNKS < p.nchunks ? c0 + BATCH_BLOCK_CHUNKS : p.nchunks;
+        if (!mttkrp_range<FT, C, D1, M_SORTED>(p, bars, carry, wbuf, nullptr, (int)c0, (int)c1, k)) return;
     }
+}
+
+// One class of tasks: kernel (C, D1), its task table and launch shape.
+struct BatchClass {
+    int C = 1, D1 = 2;
+    std::vector<BatchTask> htasks;
+    BatchTask *dtasks = nullptr;
+    int64_t total_blocks = 0;
+    int stage_words = 0;
+    int cb = 0;
+    size_t smem = 0;
+    int blocks = 0;
+};
+
+template <typename FT> const void *class_fn(int C, int D1) {
+    static const void *tab[2][4] = {
+        {(const void *)mttkrp_batch_kernel<FT, 1, 1>, (const void *)mttkrp_batch_kernel<FT, 1, 2>,
+         (const void *)mttkrp_batch_kernel<FT, 1, 3>, (const void *)mttkrp_batch_kernel<FT, 1, 4>},
+        {(const void *)mttkrp_batch_kernel<FT, 2, 1>, (const void *)mttkrp_batch_kernel<FT, 2, 2>,
+         (const void *)mttkrp_batch_kernel<FT, 2, 3>, (const void *)mttkrp_batch_kernel<FT, 2, 4>}};
+    return (C >= 1 && C <= 2 && D1 >= 1 && D1 <= 4) ? tab[C - 1][D1 - 1] : nullptr;
+}
+
+const void *batch_fn(spt_dtype fdt, int C, int D1) {
+    return fdt == SPT_F32    ? class_fn<float>(C, D1)
+           : fdt == SPT_BF16 ? class_fn<__nv_bfloat16>(C, D1)
+                             : class_fn<__half>(C, D1);
 }
 
 int ilog2i(int x) {
@@ -166,41 +123,43 @@ using namespace spt;
 
 struct spt_batch_s {
     spt_dtype fdt = SPT_F32;
-    std::vector<BatchTask> htasks;
+    std::vector<BatchClass> classes;
     std::vector<ZeroSeg> hsegs;
-    BatchTask *dtasks = nullptr;
     ZeroSeg *dsegs = nullptr;
-    unsigned long long *counter = nullptr;
+    unsigned long long *counters = nullptr;  // one per class
     int *err = nullptr;
-    int64_t total = 0;
-    int stage_words = 0;
+    int64_t ntasks = 0;
+    int64_t total_chunks = 0;
     int wpc = 8;
-    size_t smem = 0;
-    int blocks = 0;
     cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
 spt_status enqueue_batch(spt_batch b, cudaStream_t st) {
-    if (b->total == 0) return SPT_OK;
-    dim3 zg(64, (unsigned)std::min<size_t>(b->hsegs.size(), 1024));
-    batch_zero_kernel<<<zg, 256, 0, st>>>(b->dsegs, (int)b->hsegs.size(), b->counter);
+    if (b->classes.empty()) return SPT_OK;
+    dim3 zg(64, (unsigned)std::max<size_t>(1, std::min<size_t>(b->hsegs.size(), 1024)));
+    batch_zero_kernel<<<zg, 256, 0, st>>>(b->dsegs, (int)b->hsegs.size(), b->counters, (int)b->classes.size());
     SPT_LAUNCH_CHECK("batch_zero_kernel");
-    const int nt = (int)b->htasks.size();
-    if (b->fdt == SPT_F32)
-        mttkrp_batch_kernel<float><<<b->blocks, b->wpc * 32, b->smem, st>>>(
-            b->dtasks, nt, b->total, b->counter, b->stage_words, b->err);
-    else if (b->fdt == SPT_BF16)
-        mttkrp_batch_kernel<__nv_bfloat16><<<b->blocks, b->wpc * 32, b->smem, st>>>(
-            b->dtasks, nt, b->total, b->counter, b->stage_words, b->err);
-    else
-        mttkrp_batch_kernel<__half><<<b->blocks, b->wpc * 32, b->smem, st>>>(
-            b->dtasks, nt, b->total, b->counter, b->stage_words, b->err);
-    SPT_LAUNCH_CHECK("mttkrp_batch_kernel");
+    for (size_t c = 0; c < b->classes.size(); ++c) {
+        BatchClass &k = b->classes[c];
+        const BatchTask *dt = k.dtasks;
+        int nt = (int)k.htasks.size();
+        int64_t tb = k.total_blocks;
+        unsigned long long *cnt = b->counters + c;
+        int sw = k.stage_words, cb = k.cb;
+        void *args[] = {(void *)&dt, (void *)&nt, (void *)&tb, (void *)&cnt, (void *)&sw, (void *)&cb};
+        SPT_CUDA(cudaLaunchKernel(batch_fn(b->fdt, k.C, k.D1), dim3(k.blocks), dim3(b->wpc * 32), args, k.smem, st));
+    }
     return SPT_OK;
 }
 
-template <typename FT> const void *batch_fn() { return (const void *)mttkrp_batch_kernel<FT>; }
+void free_batch(spt_batch b) {
+    for (auto &k : b->classes) cudaFree(k.dtasks);
+    cudaFree(b->dsegs);
+    cudaFree(b->counters);
+    cudaFree(b->err);
+    delete b;
+}
 }  // namespace
 
 extern "C" {
@@ -214,7 +173,6 @@ spt_status mttkrp_batch_create(int count, const spt_batch_item *items, spt_dtype
     spt_batch b = new (std::nothrow) spt_batch_s();
     if (!b) return fail(SPT_ENOMEM, "mttkrp_batch_create: host allocation");
     b->fdt = fdt;
-    int64_t first = 0;
     for (int q = 0; q < count; ++q) {
         const spt_batch_item &it = items[q];
         spt_tensor t = it.tensor;
@@ -272,42 +230,54 @@ spt_status mttkrp_batch_create(int count, const spt_batch_item *items, spt_dtype
             p.S = S;
             p.npw = G * S;
             p.nchunks = (t->nnz + p.npw - 1) / p.npw;
-            p.err = nullptr;
-            tk.first_item = first;
-            tk.d1 = t->d - 1;
-            tk.C = C;
-            first += p.nchunks;
-            b->stage_words = std::max(b->stage_words, (p.npw * record_words(t->d) + 3) & ~3);
-            b->htasks.push_back(tk);
+            p.loss = -1;
             b->hsegs.push_back(ZeroSeg{o, t->dims[n] * (int64_t)it.ld});
+            ++b->ntasks;
+            if (t->nnz == 0) continue;  // zero-filled, nothing to add
+            BatchClass *cls = nullptr;
+            for (auto &k : b->classes)
+                if (k.C == C && k.D1 == t->d - 1) cls = &k;
+            if (!cls) {
+                b->classes.emplace_back();
+                cls = &b->classes.back();
+                cls->C = C;
+                cls->D1 = t->d - 1;
+            }
+            tk.first_block = cls->total_blocks;
+            cls->total_blocks += (p.nchunks + BATCH_BLOCK_CHUNKS - 1) / BATCH_BLOCK_CHUNKS;
+            cls->stage_words = std::max(cls->stage_words, p.npw * record_words(t->d));
+            cls->cb = std::max(cls->cb, carry_bytes(C, L, 4));
+            b->total_chunks += p.nchunks;
+            cls->htasks.push_back(tk);
         }
     }
-    b->total = first;
-    b->smem = 16 * (size_t)b->wpc + (size_t)b->wpc * 2 * b->stage_words * 4;
-    if (b->smem > 227 * 1024) { delete b; return fail(SPT_EINVAL, "mttkrp_batch_create: staging exceeds shared memory"); }
-    const void *fn = fdt == SPT_F32 ? batch_fn<float>() : (fdt == SPT_BF16 ? batch_fn<__nv_bfloat16>() : batch_fn<__half>());
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-    int bps = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, b->wpc * 32, b->smem);
-    if (e != cudaSuccess || bps < 1) { delete b; return e != cudaSuccess ? cuda_fail(e, "mttkrp_batch_create") : fail(SPT_EINVAL, "batch kernel does not fit"); }
-    b->blocks = bps * sm_count();
-    // device copies of the task table and zero list, counter, status word
-    e = cudaMalloc(&b->dtasks, sizeof(BatchTask) * std::max<size_t>(1, b->htasks.size()));
-    if (e == cudaSuccess) e = cudaMalloc(&b->dsegs, sizeof(ZeroSeg) * std::max<size_t>(1, b->hsegs.size()));
-    if (e == cudaSuccess) e = cudaMalloc(&b->counter, sizeof(unsigned long long));
+    cudaError_t e = cudaMalloc(&b->counters, sizeof(unsigned long long) * std::max<size_t>(1, b->classes.size()));
     if (e == cudaSuccess) e = cudaMalloc(&b->err, sizeof(int));
-    if (e == cudaSuccess && !b->htasks.empty())
-        e = cudaMemcpy(b->dtasks, b->htasks.data(), sizeof(BatchTask) * b->htasks.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dsegs, sizeof(ZeroSeg) * std::max<size_t>(1, b->hsegs.size()));
     if (e == cudaSuccess && !b->hsegs.empty())
         e = cudaMemcpy(b->dsegs, b->hsegs.data(), sizeof(ZeroSeg) * b->hsegs.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(b->err, 0, sizeof(int));
+    for (auto &k : b->classes) {
+        if (e != cudaSuccess) break;
+        k.stage_words = (k.stage_words + 3) & ~3;  // 16-byte aligned staging buffers
+        k.smem = 16 * (size_t)b->wpc + (size_t)b->wpc * k.cb + (size_t)b->wpc * 2 * k.stage_words * 4;
+        if (k.smem > 227 * 1024) { free_batch(b); return fail(SPT_EINVAL, "mttkrp_batch_create: staging exceeds shared memory"); }
+        const void *fn = batch_fn(fdt, k.C, k.D1);
+        if (!fn) { free_batch(b); return fail(SPT_EUNSUPPORTED, "mttkrp_batch_create: no kernel for this class"); }
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+        int bps = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, b->wpc * 32, k.smem);
+        if (e == cudaSuccess && bps < 1) { free_batch(b); return fail(SPT_EINVAL, "batch kernel does not fit"); }
+        k.blocks = bps * sm_count();
+        for (auto &tk : k.htasks) tk.p.err = b->err;
+        if (e == cudaSuccess) e = cudaMalloc(&k.dtasks, sizeof(BatchTask) * std::max<size_t>(1, k.htasks.size()));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(k.dtasks, k.htasks.data(), sizeof(BatchTask) * k.htasks.size(), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
-        cudaFree(b->dtasks); cudaFree(b->dsegs); cudaFree(b->counter); cudaFree(b->err);
-        delete b;
+        free_batch(b);
         return cuda_fail(e, "mttkrp_batch_create: device tables");
     }
-    for (auto &tk : b->htasks) tk.p.err = b->err;
-    cudaMemcpy(b->dtasks, b->htasks.data(), sizeof(BatchTask) * b->htasks.size(), cudaMemcpyHostToDevice);
     *out = b;
     return SPT_OK;
 }
@@ -333,9 +303,13 @@ spt_status mttkrp_batch_run(spt_batch b, void *stream) {
 
 spt_status mttkrp_batch_info(spt_batch b, int64_t *tasks, int64_t *items, int *blocks) {
     if (!b) return fail(SPT_EINVAL, "mttkrp_batch_info: NULL batch");
-    if (tasks) *tasks = (int64_t)b->htasks.size();
-    if (items) *items = b->total;
-    if (blocks) *blocks = b->blocks;
+    if (tasks) *tasks = b->ntasks;
+    if (items) *items = b->total_chunks;
+    if (blocks) {
+        int m = 0;
+        for (auto &k : b->classes) m = std::max(m, k.blocks);
+        *blocks = m;
+    }
     return SPT_OK;
 }
 
@@ -352,11 +326,7 @@ spt_status mttkrp_batch_destroy(spt_batch b) {
     if (!b) return fail(SPT_EINVAL, "mttkrp_batch_destroy: NULL batch");
     cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy(b->exec);
-    cudaFree(b->dtasks);
-    cudaFree(b->dsegs);
-    cudaFree(b->counter);
-    cudaFree(b->err);
-    delete b;
+    free_batch(b);
     return SPT_OK;
 }
 

@@ -179,11 +179,19 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
         p.prows = (int)((t->dims[mode] + K - 1) / K);
         smem += (size_t)p.prows * p.pld * ab;
     }
-    MttkrpKernelFn fn = gcp               ? gcp_kernel_fn(fdt, C, D1)
-                        : fdt == SPT_F32  ? mttkrp_kernel_f32(C, D1, kmode)
-                        : fdt == SPT_BF16 ? mttkrp_kernel_bf16(C, D1, kmode)
-                        : fdt == SPT_F64  ? mttkrp_kernel_f64(C, D1, kmode)
-                                          : mttkrp_kernel_f16(C, D1, kmode);
+    // a lane whose whole chunk lies past column R: the sorted traversal takes
+    // the clamped-gather kernels, whose gathers then do not diverge
+    const bool idle_chunks = (int64_t)p.n_rb * rb_cols - rank >= vec;
+    MttkrpKernelFn fn = gcp                 ? gcp_kernel_fn(fdt, C, D1)
+                        : (kmode == M_SORTED && idle_chunks)
+                            ? (fdt == SPT_F32    ? mttkrp_kernel_f32_clamp(C, D1)
+                               : fdt == SPT_BF16 ? mttkrp_kernel_bf16_clamp(C, D1)
+                               : fdt == SPT_F64  ? mttkrp_kernel_f64_clamp(C, D1)
+                                                 : mttkrp_kernel_f16_clamp(C, D1))
+                        : fdt == SPT_F32    ? mttkrp_kernel_f32(C, D1, kmode)
+                        : fdt == SPT_BF16   ? mttkrp_kernel_bf16(C, D1, kmode)
+                        : fdt == SPT_F64    ? mttkrp_kernel_f64(C, D1, kmode)
+                                            : mttkrp_kernel_f16(C, D1, kmode);
     if (!fn) return fail(SPT_EUNSUPPORTED, "mttkrp: no kernel for this order/chunks");
     spt_status e = ensure_smem_attr(fn, (int)smem);
     if (e) return e;
