@@ -5,6 +5,11 @@
 #include "internal.h"
 #include "mttkrp_kernel.cuh"
 
+// 0: never take the clamped-gather kernels (build variant for comparisons)
+#ifndef SPT_CLAMP_GATHERS
+#define SPT_CLAMP_GATHERS 1
+#endif
+
 namespace spt {
 
 int elem_bytes(spt_dtype fdt) { return fdt == SPT_F64 ? 8 : (fdt == SPT_F32 ? 4 : 2); }
@@ -179,9 +184,12 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
         p.prows = (int)((t->dims[mode] + K - 1) / K);
         smem += (size_t)p.prows * p.pld * ab;
     }
-    // a lane whose whole chunk lies past column R: the sorted traversal takes
-    // the clamped-gather kernels, whose gathers then do not diverge
-    const bool idle_chunks = (int64_t)p.n_rb * rb_cols - rank >= vec;
+    // a lane whose whole chunk lies past column R: with at most 8 lanes per
+    // nonzero the sorted traversal takes the clamped-gather kernels, whose
+    // gathers then do not diverge (measured: 4-way R=20 1.55x, 5-way R=20
+    // 1.12x); with 16 or 32 lanes the predicated gathers were as fast or
+    // faster (4-way R=40: 7%, the uniform 3-way R=40..56: 10%)
+    const bool idle_chunks = SPT_CLAMP_GATHERS && L <= 8 && (int64_t)p.n_rb * rb_cols - rank >= vec;
     MttkrpKernelFn fn = gcp                 ? gcp_kernel_fn(fdt, C, D1)
                         : (kmode == M_SORTED && idle_chunks)
                             ? (fdt == SPT_F32    ? mttkrp_kernel_f32_clamp(C, D1)
