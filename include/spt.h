@@ -327,20 +327,22 @@ typedef struct {
     const spt_schedule *scheds;
 } spt_batch_item;
 
-/* Build a batch: one task per (tensor, mode), whose chunks of nonzeros form
- * one work list.  Copies the task table to the device (synchronous); the
- * pointers are captured, so the tensors, factors and outputs must outlive
- * the batch and keep their addresses. */
+/* Build a batch: one task per (tensor, mode); tasks are grouped by kernel
+ * class (chunks per lane, order), and each class's task chunks, cut into
+ * blocks of 8, form its work list.  Copies the task tables to the device
+ * (synchronous); the pointers are captured, so the tensors, factors and
+ * outputs must outlive the batch and keep their addresses. */
 spt_status mttkrp_batch_create(int count, const spt_batch_item *items, spt_dtype fdt, spt_batch *out);
 
-/* Run every task: one zero-fill kernel for the outputs, then one persistent
- * kernel whose warps claim chunks from a device counter.  On a non-default
- * stream the two launches are captured in a CUDA graph at the first call and
- * replayed afterwards; on the legacy default stream they are launched
- * directly. */
+/* Run every task: one zero-fill kernel for the outputs and counters, then
+ * one persistent kernel per class whose warps claim blocks of chunks from
+ * the class's device counter.  On a non-default stream the launches are
+ * captured in a CUDA graph at the first call and replayed afterwards; on the
+ * legacy default stream they are launched directly. */
 spt_status mttkrp_batch_run(spt_batch b, void *stream);
 
-/* Tasks, work items (chunks) and persistent CTAs of a batch. Host outputs. */
+/* Tasks, work items (chunks) and persistent CTAs (the largest class's grid)
+ * of a batch.  Host outputs. */
 spt_status mttkrp_batch_info(spt_batch b, int64_t *tasks, int64_t *items, int *blocks);
 
 /* Synchronise `stream` and read the batch kernel's status word (SPT_ETIMEOUT

@@ -195,3 +195,38 @@ def test_trained_selector_gains_over_fixed_rules_on_unseen_tensors():
           f"default rule {t_dflt:.2f} ms")
     assert t_sel <= 1.10 * t_best
     assert t_sel < t_paper
+
+
+def test_batched_mixed_kernel_classes():
+    """One batch whose tasks fall into several kernel classes (orders 3 and
+    4, one and two chunks per lane via R = 136) and blocks of chunks that
+    split tasks unevenly; results against the oracle and single launches."""
+    P = _lib()
+    cases = [((700, 300, 90), 20_003, 136), ((500, 60, 40, 9), 30_011, 24), ((900, 800, 700), 7, 16)]
+    tensors, items, facs_all, outs_all, host = [], [], [], [], []
+    for q, (dims, nnz, R) in enumerate(cases):
+        idx, vals = synth.coo_zipf(dims, nnz, 1.1, 60 + q)
+        T = P.SparseTensor(idx, vals, dims)
+        T.build_permutation()
+        facs_np = synth.factor_matrices(dims, R, 70 + q, "normal")
+        facs = [to_device_factor(f, "f32") for f in facs_np]
+        outs = [torch.full((I, facs[0].shape[1]), 3.0, device="cuda") for I in dims]
+        tensors.append(T); facs_all.append(facs); outs_all.append(outs); host.append((idx, vals, facs_np, dims, R))
+        items.append({"tensor": T.handle, "mode": -1, "rank": R, "ld": facs[0].shape[1],
+                      "factors": [f.data_ptr() for f in facs], "outs": [o.data_ptr() for o in outs]})
+    b, keep = P.mttkrp_batch_create(items, "f32")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            P.mttkrp_batch_run(b, s.cuda_stream)
+    torch.cuda.synchronize()
+    P.mttkrp_batch_check(b)
+    for T, facs, outs, (idx, vals, facs_np, dims, R) in zip(tensors, facs_all, outs_all, host):
+        for n in range(len(dims)):
+            got = outs[n].cpu().numpy()
+            assert np.all(got[:, R:] == 0)
+            ref = oracle.mttkrp(idx, vals, dims, [widen(f, "f32", R) for f in facs_np], n, R)
+            assert rel_fro(got[:, :R], ref) <= 1e-5, (dims, n)
+    P.mttkrp_batch_destroy(b)
+    for T in tensors:
+        T.close()
