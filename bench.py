@@ -459,6 +459,37 @@ def measure_extras(args, P, torch, w, T, idx, vals, facs_np, dtype, R, d, ld, ou
                                   "rel_err_sampled_rows": errs or None}
         del fd
     out["variants"] = var
+    # ---- deterministic sums (per-warp boundary slots and a fix-up kernel in
+    # place of the boundary rows' atomics): ms per mode, bit-identical repeats
+    if args.scatter == "sorted" and R <= 256:
+        fnp = w.factors(R, dtype)
+        fd = [_dev_factor(torch, f, dtype) for f in fnp]
+        A64 = [oracle.as_f64(f, dtype)[:, :R].copy() for f in fnp]
+        ms, errs, same = [], [], True
+        for n in range(d):
+            s = sched_for(n, "sorted", dtype)
+            if s is not None and s.lanes_per_nnz * s.chunks * 4 < R:
+                s = None
+            T.mttkrp(n, fd, R, out=outs[n], sched=s, deterministic=True)
+            first = outs[n].clone()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                T.mttkrp(n, fd, R, out=outs[n], sched=s, deterministic=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1) / 3)
+            iv = torch.int64 if first.dtype == torch.float64 else torch.int32
+            same = same and torch.equal(first.view(iv), outs[n].view(iv))
+            rows = sampled_rows(w, idx, n, R)
+            got = outs[n][torch.from_numpy(rows).long().cuda(), :R].double().cpu().numpy()
+            ref = oracle.mttkrp_rows(idx, vals, w.dims, A64, n, R, rows)
+            errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+        out["deterministic"] = {"ms_per_mode": ms, "nnzR_per_s": w.nnz * R * d / (sum(ms) / 1e3),
+                                "vs_default_ms": sum(ms) / sum(mode_ms), "bit_identical_repeats": same,
+                                "rel_err_sampled_rows": errs}
+        del fd
     # ---- generalised CP gradient (one fused launch per mode + the Poisson
     # dense term), beside the plain MTTKRP of the same schedule
     if args.scatter != "perm" and d >= 2:

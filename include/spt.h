@@ -202,6 +202,22 @@ spt_status mttkrp(spt_tensor t, int mode, const void *const *factors, spt_dtype 
                   int ld, const void *lambda, void *out, const spt_schedule *sched,
                   void *stream);
 
+/* Deterministic mode-n MTTKRP: arguments and result as mttkrp(), but the
+ * sums are added in an order fixed by the tensor, the schedule and the GPU's
+ * SM count, so repeated calls give bit-identical out.  The sorted traversal
+ * with one rank block: rows inside a warp's range of nonzeros have one
+ * writer; the two boundary rows of each range are written to per-warp slots
+ * (scratch allocated and freed on `stream`) and a second kernel stores each
+ * such row as the sum of its slots in warp order, in place of atomics.
+ *  sched : NULL = the library's schedule made sorted (lanes widened to 32 if
+ *          needed); else SPT_SCATTER_SORTED with lanes_per_nnz * chunks * 4
+ *          >= rank (SPT_EINVAL otherwise).
+ * SPT_ESTATE without the mode-sorted copy (build_mode_permutation);
+ * SPT_EUNSUPPORTED for rank > 256. */
+spt_status mttkrp_deterministic(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt,
+                                int rank, int ld, const void *lambda, void *out,
+                                const spt_schedule *sched, void *stream);
+
 /* Record the schedule to use for (mode, fdt, rank) wherever no schedule is
  * passed (mttkrp with sched == NULL, cp_als_step), e.g. one chosen by
  * mttkrp_autotune or mttkrp_select.  s == NULL clears it.  The schedule is

@@ -93,6 +93,8 @@ _sig("build_mode_permutation", _vp, C.c_int, C.c_int, _vp)
 _sig("tensor_get_permutation", _vp, C.c_int, _vp, _vp)
 _sig("mttkrp", _vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _vp, _vp,
      C.POINTER(spt_schedule), _vp)
+_sig("mttkrp_deterministic", _vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _vp, _vp,
+     C.POINTER(spt_schedule), _vp)
 _sig("mttkrp_default_schedule", _vp, C.c_int, C.c_int, C.c_int, C.POINTER(spt_schedule))
 _sig("tensor_set_schedule", _vp, C.c_int, C.c_int, C.c_int, C.POINTER(spt_schedule))
 _sig("mttkrp_paper_sizes", C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int))
@@ -103,7 +105,7 @@ _sig("spt_fma_probe", C.c_int, C.c_int64, _vp, C.POINTER(C.c_double), _vp)
 
 EXPORTED = ["spt_last_error", "spt_device_info", "tensor_create_coo", "tensor_destroy",
             "tensor_info", "tensor_get_coo", "tensor_norm2", "tensor_check",
-            "build_mode_permutation", "tensor_get_permutation", "mttkrp",
+            "build_mode_permutation", "tensor_get_permutation", "mttkrp", "mttkrp_deterministic",
             "mttkrp_default_schedule", "tensor_set_schedule", "mttkrp_paper_sizes", "mttkrp_paper_schedule",
             "spt_stream_copy", "spt_convert_f32", "spt_fma_probe"]
 
@@ -228,6 +230,13 @@ def mttkrp(t: int, mode: int, factor_ptrs: Sequence[Optional[int]], fdt, rank: i
            stream: int = 0):
     _chk(_L.mttkrp(t, mode, _ptrs(factor_ptrs), _dt(fdt), rank, ld, lambda_ptr or None, out_ptr,
                    C.byref(sched) if sched is not None else None, stream or None))
+
+
+def mttkrp_deterministic(t: int, mode: int, factor_ptrs: Sequence[Optional[int]], fdt, rank: int, ld: int,
+                         lambda_ptr: Optional[int], out_ptr: int, sched: Optional[spt_schedule] = None,
+                         stream: int = 0):
+    _chk(_L.mttkrp_deterministic(t, mode, _ptrs(factor_ptrs), _dt(fdt), rank, ld, lambda_ptr or None,
+                                 out_ptr, C.byref(sched) if sched is not None else None, stream or None))
 
 
 def mttkrp_default_schedule(t: int, mode: int, fdt, rank: int) -> spt_schedule:

@@ -237,9 +237,9 @@ spt_status tensor_check(spt_tensor t, void *stream) {
     return SPT_OK;
 }
 
-spt_status mttkrp(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt, int rank,
-                  int ld, const void *lambda, void *out, const spt_schedule *sched,
-                  void *stream) {
+static spt_status mttkrp_impl(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt, int rank,
+                              int ld, const void *lambda, void *out, const spt_schedule *sched,
+                              void *stream, bool det) {
     if (!t) return fail(SPT_EINVAL, "mttkrp: NULL tensor");
     if (mode < 0 || mode >= t->d) return fail(SPT_EINVAL, "mttkrp: mode out of range");
     if (t->d > SPT_MAX_KERNEL_ORDER) return fail(SPT_EUNSUPPORTED, "mttkrp: order > 5");
@@ -259,9 +259,35 @@ spt_status mttkrp(spt_tensor t, int mode, const void *const *factors, spt_dtype 
     }
     spt_schedule s = sched ? *sched : default_schedule(t, mode, fdt, rank);
     if (s.scatter == SPT_SCATTER_AUTO) s.scatter = default_schedule(t, mode, fdt, rank).scatter;
+    if (det) {
+        if (!t->sorted_buf[mode])
+            return fail(SPT_ESTATE, "mttkrp_deterministic: needs the mode-sorted copy (build_mode_permutation)");
+        if (rank > 256) return fail(SPT_EUNSUPPORTED, "mttkrp_deterministic: rank must be <= 256");
+        if (!sched) {  // a recorded schedule of another kind: keep its sizes where they fit
+            s.scatter = SPT_SCATTER_SORTED;
+            if (s.lanes_per_nnz * s.chunks * 4 < rank) {
+                s.lanes_per_nnz = 32;
+                s.chunks = rank > 128 ? 2 : 1;
+            }
+        }
+        if (s.scatter != SPT_SCATTER_SORTED || s.lanes_per_nnz * s.chunks * 4 < rank)
+            return fail(SPT_EINVAL, "mttkrp_deterministic: the schedule must be sorted with lanes x chunks x 4 >= rank");
+    }
     spt_status c = check_schedule(t, mode, fdt, rank, s);
     if (c) return c;
-    return launch_mttkrp(t, mode, factors, fdt, rank, ld, lambda, out, s, (cudaStream_t)stream);
+    return launch_mttkrp(t, mode, factors, fdt, rank, ld, lambda, out, s, (cudaStream_t)stream, nullptr, det);
+}
+
+spt_status mttkrp(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt, int rank,
+                  int ld, const void *lambda, void *out, const spt_schedule *sched,
+                  void *stream) {
+    return mttkrp_impl(t, mode, factors, fdt, rank, ld, lambda, out, sched, stream, false);
+}
+
+spt_status mttkrp_deterministic(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt, int rank,
+                                int ld, const void *lambda, void *out, const spt_schedule *sched,
+                                void *stream) {
+    return mttkrp_impl(t, mode, factors, fdt, rank, ld, lambda, out, sched, stream, true);
 }
 
 spt_status tensor_set_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank, const spt_schedule *s) {

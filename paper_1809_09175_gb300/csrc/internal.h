@@ -26,10 +26,13 @@ struct GcpArgs {
 
 // MTTKRP launch with an explicit (validated) schedule; out is zeroed here.
 // With gcp != NULL the launch runs the generalised CP gradient kernel
-// instead (sorted traversal, one rank block).
+// instead (sorted traversal, one rank block).  det: deterministic sums (sorted
+// traversal, one rank block): the rows a warp shares with its neighbours go
+// to per-warp slots that a second kernel adds in slot order.
 spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt,
                          int rank, int ld, const void *lambda, void *out,
-                         const spt_schedule &sched, cudaStream_t st, const GcpArgs *gcp = nullptr);
+                         const spt_schedule &sched, cudaStream_t st, const GcpArgs *gcp = nullptr,
+                         bool det = false);
 spt_status check_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank,
                           const spt_schedule &s);
 spt_schedule default_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank);

@@ -16,6 +16,106 @@ int elem_bytes(spt_dtype fdt) { return fdt == SPT_F64 ? 8 : (fdt == SPT_F32 ? 4 
 int acc_bytes(spt_dtype fdt) { return fdt == SPT_F64 ? 8 : 4; }
 
 namespace {
+// Deterministic sums: out(row, :) = the sum of the slots holding `row` (slot
+// rows are non-decreasing where set, -1 where unused; a row held by a slot
+// receives no other write).  One warp per slot i, working when i starts its
+// row's run of slots: a run of at most 8 slots is added in slot order, one
+// lane per column quad; a longer run (a hot row spread over many warps'
+// ranges) is split over the lanes (lane t takes slots i+t, i+t+32, ...) and
+// the lanes' sums are combined by a fixed shuffle tree.  The order of every
+// addition depends on the slot layout only, never on timing.
+template <typename AT>
+__global__ void __launch_bounds__(256) det_fixup_kernel(const int *__restrict__ rows, const AT *__restrict__ vals,
+                                                        int nslots, int R, int64_t old, AT *out) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int q4 = (R + 3) / 4;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nslots; i += nw) {
+        const int row = rows[i];  // warp-uniform from here on
+        if (row < 0) continue;
+        int prev = i - 1;
+        while (prev >= 0 && rows[prev] < 0) --prev;
+        if (prev >= 0 && rows[prev] == row) continue;  // not the first slot of this row
+        int end = nslots;  // the first slot past i holding another row
+        for (int k0 = i + 1; k0 < nslots; k0 += 32) {
+            const int k = k0 + lane;
+            const int rk = k < nslots ? rows[k] : -1;
+            const unsigned b = __ballot_sync(FULL, rk >= 0 && rk != row);
+            if (b) {
+                end = k0 + __ffs(b) - 1;
+                break;
+            }
+        }
+        AT *dst = out + (int64_t)row * old;
+        if (end - i <= 8) {
+            for (int q = lane; q < q4; q += 32) {
+                AT sum[4] = {(AT)0, (AT)0, (AT)0, (AT)0};
+                for (int k = i; k < end; ++k) {
+                    if (rows[k] != row) continue;  // an unused slot
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) sum[v] += vals[(int64_t)k * old + 4 * q + v];
+                }
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (4 * q + v < R) dst[4 * q + v] = sum[v];
+            }
+            continue;
+        }
+        for (int q = 0; q < q4; ++q) {
+            AT sum[4] = {(AT)0, (AT)0, (AT)0, (AT)0};
+            for (int k = i + lane; k < end; k += 32) {
+                if (rows[k] != row) continue;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) sum[v] += vals[(int64_t)k * old + 4 * q + v];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) sum[v] += __shfl_down_sync(FULL, sum[v], o);
+            if (lane == 0) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (4 * q + v < R) dst[4 * q + v] = sum[v];
+            }
+        }
+    }
+}
+
+// Deterministic sums: the kernel writes the two boundary rows of each warp's
+// range (row id, partial row) into slots 2w and 2w+1 of a scratch array;
+// det_fixup_kernel then stores each such row as the sum of its slots.  Every
+// other row has one writer, so the result does not depend on the order in
+// which warps finish.
+spt_status launch_det(MttkrpKernelFn fn, MttkrpParams p, int blocks, int wpc, size_t smem, int ab,
+                      cudaStream_t st) {
+    const int nslots = 2 * blocks * wpc;
+    const size_t rows_bytes = ((size_t)nslots * sizeof(int) + 255) & ~(size_t)255;
+    void *buf = nullptr;
+    spt_status c = dmalloc(&buf, rows_bytes + (size_t)nslots * p.old * ab, st);
+    if (c) return c;
+    p.det_rows = reinterpret_cast<int *>(buf);
+    p.det_vals = reinterpret_cast<char *>(buf) + rows_bytes;
+    cudaError_t e = cudaMemsetAsync(p.det_rows, 0xff, (size_t)nslots * sizeof(int), st);  // -1: unused
+    if (e == cudaSuccess) {
+        fn<<<blocks, wpc * 32, smem, st>>>(p);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        const int fb = std::max(1, std::min((nslots + 7) / 8, sm_count() * 16));  // a warp per slot
+        if (ab == 8)
+            det_fixup_kernel<double><<<fb, 256, 0, st>>>(p.det_rows, (const double *)p.det_vals, nslots, p.R, p.old,
+                                                         (double *)p.out);
+        else
+            det_fixup_kernel<float><<<fb, 256, 0, st>>>(p.det_rows, (const float *)p.det_vals, nslots, p.R, p.old,
+                                                        (float *)p.out);
+        e = cudaGetLastError();
+    }
+    dfree(buf, st);
+    if (e != cudaSuccess) return cuda_fail(e, "mttkrp deterministic launch");
+    return SPT_OK;
+}
+
 int ilog2(int x) {
     int r = 0;
     while ((1 << r) < x) ++r;
@@ -115,7 +215,7 @@ spt_status check_schedule(spt_tensor t, int mode, spt_dtype fdt, int rank, const
 
 spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt,
                          int rank, int ld, const void *lambda, void *out,
-                         const spt_schedule &s, cudaStream_t st, const GcpArgs *gcp) {
+                         const spt_schedule &s, cudaStream_t st, const GcpArgs *gcp, bool det) {
     const int vec = 4;  // columns per lane chunk
     const int L = s.lanes_per_nnz, C = s.chunks;
     const int G = 32 / L;
@@ -165,6 +265,8 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
         p.loss = gcp->loss;
         p.loss_out = gcp->loss_out;
     }
+    if (det && (gcp || kmode != M_SORTED || p.n_rb != 1))
+        return fail(SPT_EINVAL, "mttkrp: deterministic sums need the sorted traversal and one rank block");
 
     const int wpe = kmode == M_PERM ? 1 : (kmode == M_SORTED ? record_words(t->d) : D1 + 2);
     size_t smem = warp_smem_bytes(wpc, C, L, ab, wpe, npw);
@@ -191,6 +293,10 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
     // faster (4-way R=40: 7%, the uniform 3-way R=40..56: 10%)
     const bool idle_chunks = SPT_CLAMP_GATHERS && L <= 8 && (int64_t)p.n_rb * rb_cols - rank >= vec;
     MttkrpKernelFn fn = gcp                 ? gcp_kernel_fn(fdt, C, D1)
+                        : det               ? (fdt == SPT_F32    ? mttkrp_kernel_f32_det(C, D1)
+                                               : fdt == SPT_BF16 ? mttkrp_kernel_bf16_det(C, D1)
+                                               : fdt == SPT_F64  ? mttkrp_kernel_f64_det(C, D1)
+                                                                 : mttkrp_kernel_f16_det(C, D1))
                         : (kmode == M_SORTED && idle_chunks)
                             ? (fdt == SPT_F32    ? mttkrp_kernel_f32_clamp(C, D1)
                                : fdt == SPT_BF16 ? mttkrp_kernel_bf16_clamp(C, D1)
@@ -233,6 +339,7 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
     const int cps = s.ctas_per_sm > 0 ? std::min(s.ctas_per_sm, bps) : bps;
     const int64_t need = (p.nchunks + wpc - 1) / wpc;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)cps * sm_count(), need));
+    if (det) return launch_det(fn, p, blocks, wpc, smem, ab, st);
     fn<<<blocks, wpc * 32, smem, st>>>(p);
     SPT_LAUNCH_CHECK("mttkrp_kernel launch");
     return SPT_OK;

@@ -84,6 +84,12 @@ struct MttkrpParams {
     int pld;      // private row stride in accumulator elements, R rounded up to 4
     int log2K;    // cluster size K = 1 << log2K CTAs share the rows
     int prows;    // private rows per CTA = ceil(In / K)
+    // deterministic sums (sorted traversal with the run carry): the first and
+    // last row of warp gw's range go to slots 2 gw and 2 gw + 1 (row ids,
+    // partial rows of stride old) instead of atomics; a fix-up kernel adds the
+    // slots of each row in an order fixed by the slot layout (DET kernels only)
+    int *det_rows;
+    void *det_vals;
     // generalised CP gradient (gcp kernels only)
     const void *fac_n;   // the mode's own factor A^(n): the model value needs it
     int loss;            // 0 Poisson (stored part), 1 Bernoulli-logit, 2 Gaussian
@@ -149,7 +155,7 @@ __device__ __forceinline__ void chunk_bounds(const MttkrpParams &p, const int32_
 // chunk's last open run is handed over instead of written, the carried run of
 // the previous chunk joins this chunk's first run, and the shared rows are the
 // range's first and last rows from the carry header.
-template <typename FT, int C, int D1, int MODE, bool GCP = false, bool CLAMP = false>
+template <typename FT, int C, int D1, int MODE, bool GCP = false, bool CLAMP = false, bool DET = false>
 __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_t *buf, int n, int b0,
                                              int b1, unsigned char *carry, typename Elem<FT>::Acc *priv,
                                              double *lacc = nullptr) {
@@ -207,8 +213,9 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
         int cur = -1, frow = -1;
         bool fclosed = false;
 
-        // emit a finished row sum: atomic for shared rows, plain store otherwise
-        auto write_row = [&](int row, AT (&a)[C][VEC], bool atomic) {
+        // emit a finished row sum: atomic for shared rows, plain store otherwise;
+        // dslot: the range's boundary slot of a shared row (0 first, 1 last)
+        auto write_row = [&](int row, AT (&a)[C][VEC], bool atomic, int dslot = -1) {
             if (MODE == M_PRIVATE) {  // add into the owning CTA's private copy
                 const int K = 1 << p.log2K;
                 AT *prow = priv + (int64_t)(row >> p.log2K) * p.pld;
@@ -229,6 +236,12 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
                 return;
             }
             AT *dst = reinterpret_cast<AT *>(p.out) + (int64_t)row * p.old;
+            if (DET && atomic && dslot >= 0) {  // deterministic: this warp's slot
+                const int slot = 2 * (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) + dslot;
+                dst = reinterpret_cast<AT *>(p.det_vals) + (int64_t)slot * p.old;
+                if (l == 0) p.det_rows[slot] = row;
+                atomic = false;
+            }
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 if (nv[c] == 0) continue;
@@ -449,7 +462,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) T[c][v] += cin[c][v];
                 }
-                if (g == 0 && crow >= 0 && first != crow) write_row(crow, cin, shared_row(crow));
+                if (g == 0 && crow >= 0 && first != crow) write_row(crow, cin, shared_row(crow), crow == s1);
                 for (int off = 1; off < G; off <<= 1) {
                     const int fu = __shfl_up_sync(FULL, f, off * L);
 #pragma unroll
@@ -478,12 +491,12 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
 #pragma unroll
                             for (int v = 0; v < VEC; ++v) facc[c][v] += Sp[c][v];
                     }
-                    write_row(frow, facc, shared_row(frow));
+                    write_row(frow, facc, shared_row(frow), frow == s1);
                 }
                 if (g < G - 1) {
-                    if (nf != cur) write_row(cur, T, shared_row(cur));  // the chain ends here
+                    if (nf != cur) write_row(cur, T, shared_row(cur), cur == s1);  // the chain ends here
                 } else if (!carry) {
-                    write_row(cur, T, shared_row(cur));
+                    write_row(cur, T, shared_row(cur), cur == s1);
                 }
                 if (carry) {
                     __syncwarp();  // every lane has read the carry
@@ -508,7 +521,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
             int orow = carry ? *crow_p : -1;
             const bool writer = (g == 0);
             auto emit = [&](int row, AT (&a)[C][VEC]) {
-                if (writer) write_row(row, a, shared_row(row));
+                if (writer) write_row(row, a, shared_row(row), row == s1);
             };
             for (int g2 = 0; g2 < G; ++g2) {
                 const int srcl = (g2 << log2L) | l;
@@ -570,7 +583,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
 }
 
 // Atomically add a carried row sum (rank block 0) to the output.
-template <typename FT, int C>
+template <typename FT, int C, bool DET = false>
 __device__ __forceinline__ void flush_carry(const MttkrpParams &p, const unsigned char *carry) {
     constexpr int VEC = Elem<FT>::VEC;
     using AT = typename Elem<FT>::Acc;
@@ -581,6 +594,12 @@ __device__ __forceinline__ void flush_carry(const MttkrpParams &p, const unsigne
     const int l = lane & (L - 1);
     const AT *acc = reinterpret_cast<const AT *>(carry + 16) + l * (C * VEC);
     AT *dst = reinterpret_cast<AT *>(p.out) + (int64_t)row * p.old;
+    constexpr bool det = DET;  // the range's last row goes to the warp's slot 1
+    if (det) {
+        const int slot = 2 * (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) + 1;
+        dst = reinterpret_cast<AT *>(p.det_vals) + (int64_t)slot * p.old;
+        if (l == 0) p.det_rows[slot] = row;
+    }
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const int col = (c * L + l) * VEC;
@@ -593,7 +612,10 @@ __device__ __forceinline__ void flush_carry(const MttkrpParams &p, const unsigne
                                                           : (AT)1)
                           : (AT)0;
 #pragma unroll
-        for (int q = 0; q < VEC; q += 4) red_add4(dst + col + q, w + q);
+        for (int q = 0; q < VEC; q += 4) {
+            if (det) store4(dst + col + q, w + q);
+            else red_add4(dst + col + q, w + q);
+        }
     }
 }
 
@@ -762,7 +784,7 @@ __device__ __forceinline__ bool mttkrp_range(const MttkrpParams &p, uint64_t *ba
 // kept as one body for the single-tensor launch, where the register
 // allocator spills less than through mttkrp_range's interface (measured:
 // 4-way R=64 13% faster).
-template <typename FT, int C, int D1, int MODE, bool GCP = false, bool CLAMP = false>
+template <typename FT, int C, int D1, int MODE, bool GCP = false, bool CLAMP = false, bool DET = false>
 __device__ __forceinline__ void mttkrp_warp_range(const MttkrpParams &p, unsigned char *smem_raw,
                                                   typename Elem<FT>::Acc *priv) {
     using AT = typename Elem<FT>::Acc;
@@ -887,11 +909,11 @@ __device__ __forceinline__ void mttkrp_warp_range(const MttkrpParams &p, unsigne
         __syncwarp();
 
         if (use_carry) {
-            mttkrp_chunk<FT, C, D1, MODE, GCP, CLAMP>(p, buf, n, -1, -1, carry, nullptr, &lacc);
+            mttkrp_chunk<FT, C, D1, MODE, GCP, CLAMP, DET>(p, buf, n, -1, -1, carry, nullptr, &lacc);
         } else {
             int b0, b1;
             chunk_bounds<D1, MODE>(p, buf, n, b0, b1);
-            mttkrp_chunk<FT, C, D1, MODE, GCP, CLAMP>(p, buf, n, b0, b1, nullptr, priv, &lacc);
+            mttkrp_chunk<FT, C, D1, MODE, GCP, CLAMP, DET>(p, buf, n, b0, b1, nullptr, priv, &lacc);
         }
 
         __syncwarp();  // every lane is done with this stage before it is refilled
@@ -902,7 +924,7 @@ __device__ __forceinline__ void mttkrp_warp_range(const MttkrpParams &p, unsigne
     }
     if (use_carry) {
         __syncwarp();
-        flush_carry<FT, C>(p, carry);
+        flush_carry<FT, C, DET>(p, carry);
     }
     if (GCP && p.loss_out) {
         for (int o = 16; o > 0; o >>= 1) lacc += __shfl_xor_sync(FULL, lacc, o);
@@ -939,11 +961,11 @@ __device__ __forceinline__ void flush_private(const MttkrpParams &p, const AT *p
     }
 }
 
-template <typename FT, int C, int D1, int MODE, bool CLAMP = false>
+template <typename FT, int C, int D1, int MODE, bool CLAMP = false, bool DET = false>
 __global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(const MttkrpParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (MODE != M_PRIVATE) {
-        mttkrp_warp_range<FT, C, D1, MODE, false, CLAMP>(p, smem_raw, nullptr);
+        mttkrp_warp_range<FT, C, D1, MODE, false, CLAMP, DET>(p, smem_raw, nullptr);
         return;
     }
     // Privatised scatter: zero this CTA's rows, wait until every CTA of the
@@ -978,6 +1000,12 @@ MttkrpKernelFn mttkrp_kernel_f32_clamp(int C, int D1);
 MttkrpKernelFn mttkrp_kernel_bf16_clamp(int C, int D1);
 MttkrpKernelFn mttkrp_kernel_f16_clamp(int C, int D1);
 MttkrpKernelFn mttkrp_kernel_f64_clamp(int C, int D1);
+// sorted traversal with the run carry whose shared rows go to per-warp slots
+// (deterministic sums; see det_fixup_kernel)
+MttkrpKernelFn mttkrp_kernel_f32_det(int C, int D1);
+MttkrpKernelFn mttkrp_kernel_bf16_det(int C, int D1);
+MttkrpKernelFn mttkrp_kernel_f16_det(int C, int D1);
+MttkrpKernelFn mttkrp_kernel_f64_det(int C, int D1);
 // Generalised CP gradient kernels: fdt in {F32, BF16, F16}, C in {1,2}, D1 in 1..4.
 MttkrpKernelFn gcp_kernel_fn(spt_dtype fdt, int C, int D1);
 
@@ -1003,6 +1031,17 @@ MttkrpKernelFn gcp_kernel_fn(spt_dtype fdt, int C, int D1);
              mttkrp_kernel<FT, 1, 3, 1, true>, mttkrp_kernel<FT, 1, 4, 1, true>},                                                \
             {mttkrp_kernel<FT, 2, 0, 1, true>, mttkrp_kernel<FT, 2, 1, 1, true>, mttkrp_kernel<FT, 2, 2, 1, true>,               \
              mttkrp_kernel<FT, 2, 3, 1, true>, mttkrp_kernel<FT, 2, 4, 1, true>}};                                               \
+        if (C < 1 || C > 2 || D1 < 0 || D1 > 4) return nullptr;                                                                  \
+        return tab[C - 1][D1];                                                                                                   \
+    } \
+    MttkrpKernelFn NAME##_det(int C, int D1) {                                                                                   \
+        static const MttkrpKernelFn tab[2][5] = {                                                                                \
+            {mttkrp_kernel<FT, 1, 0, 1, false, true>, mttkrp_kernel<FT, 1, 1, 1, false, true>,                                   \
+             mttkrp_kernel<FT, 1, 2, 1, false, true>, mttkrp_kernel<FT, 1, 3, 1, false, true>,                                   \
+             mttkrp_kernel<FT, 1, 4, 1, false, true>},                                                                           \
+            {mttkrp_kernel<FT, 2, 0, 1, false, true>, mttkrp_kernel<FT, 2, 1, 1, false, true>,                                   \
+             mttkrp_kernel<FT, 2, 2, 1, false, true>, mttkrp_kernel<FT, 2, 3, 1, false, true>,                                   \
+             mttkrp_kernel<FT, 2, 4, 1, false, true>}};                                                                          \
         if (C < 1 || C > 2 || D1 < 0 || D1 > 4) return nullptr;                                                                  \
         return tab[C - 1][D1];                                                                                                   \
     }

@@ -91,7 +91,10 @@ class SparseTensor:
 
     def mttkrp(self, mode: int, factors: List[Optional[torch.Tensor]], rank: int,
                lam: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
-               sched: Optional[B.spt_schedule] = None) -> torch.Tensor:
+               sched: Optional[B.spt_schedule] = None, deterministic: bool = False) -> torch.Tensor:
+        """Mode-n MTTKRP into out (allocated if None).  deterministic=True
+        runs mttkrp_deterministic: bit-identical results from call to call
+        (needs build_permutation)."""
         f0 = next(f for m, f in enumerate(factors) if m != mode and f is not None) \
             if self.order > 1 else None
         ld = f0.shape[1] if f0 is not None else factor_ld(rank)
@@ -100,8 +103,9 @@ class SparseTensor:
             out = torch.empty((self.dims[mode], ld), device="cuda",
                               dtype=torch.float64 if fdt == "f64" else torch.float32)
         ptrs = [0 if (m == mode or f is None) else f.data_ptr() for m, f in enumerate(factors)]
-        B.mttkrp(self.handle, mode, ptrs, fdt, rank, ld,
-                 lam.data_ptr() if lam is not None else 0, out.data_ptr(), sched, _stream())
+        fn = B.mttkrp_deterministic if deterministic else B.mttkrp
+        fn(self.handle, mode, ptrs, fdt, rank, ld,
+           lam.data_ptr() if lam is not None else 0, out.data_ptr(), sched, _stream())
         return out
 
     def gcp_gradient(self, mode: int, factors: List[torch.Tensor], rank: int, loss: str,
