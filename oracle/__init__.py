@@ -31,6 +31,9 @@ def lib():
         L = C.CDLL(path)
         L.oracle_mttkrp.argtypes = [C.c_int, _lp, C.c_int64, _ip, _dp, C.c_int, C.c_int,
                                     C.POINTER(_dp), _lp, _dp, _dp, C.c_int64]
+        L.oracle_mttkrp_threads.argtypes = [C.c_int, _lp, C.c_int64, _ip, _dp, C.c_int, C.c_int,
+                                            C.POINTER(_dp), _lp, _dp, _dp, C.c_int64, C.c_int]
+        L.oracle_mttkrp_threads.restype = C.c_int
         L.oracle_mttkrp_rows.argtypes = [C.c_int, _lp, C.c_int64, _ip, _dp, C.c_int, C.c_int,
                                          C.POINTER(_dp), _lp, _dp, C.c_int64, _ip, _dp, C.c_int64]
         L.oracle_stable_argsort.argtypes = [C.c_int64, _ip, _ip]
@@ -101,6 +104,24 @@ def mttkrp(idx, vals, dims, factors, n: int, R: int, lam=None, ld: Optional[int]
     lam_a = None if lam is None else np.ascontiguousarray(lam, dtype=np.float64)
     lib().oracle_mttkrp(d, _l(dims_a), P, _i(idx), _d(vals), n, R, arr, _l(lda),
                         None if lam_a is None else _d(lam_a), _d(V), ld)
+    return V
+
+
+def mttkrp_threads(idx, vals, dims, factors, n: int, R: int, threads: int, lam=None,
+                   ld: Optional[int] = None):
+    """The MTTKRP definition on ``threads`` host threads: contiguous nonzero
+    ranges into private arrays, added in thread order (the CPU baseline's
+    all-core form; ``threads=1`` is ``mttkrp`` operation for operation)."""
+    idx, vals = _prep(idx, vals)
+    d, P = idx.shape
+    dims_a = np.array(dims, dtype=np.int64)
+    fs, arr, lda = _fac_ptrs(factors)
+    ld = R if ld is None else ld
+    V = np.zeros((int(dims[n]), ld), dtype=np.float64)
+    lam_a = None if lam is None else np.ascontiguousarray(lam, dtype=np.float64)
+    if lib().oracle_mttkrp_threads(d, _l(dims_a), P, _i(idx), _d(vals), n, R, arr, _l(lda),
+                                   None if lam_a is None else _d(lam_a), _d(V), ld, int(threads)):
+        raise MemoryError("oracle_mttkrp_threads: thread or array creation failed")
     return V
 
 

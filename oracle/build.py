@@ -20,7 +20,7 @@ def build(force: bool = False) -> str:
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", SRC, "-o", tmp, "-lm"]
+           "-pthread", "-shared", SRC, "-o", tmp, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB

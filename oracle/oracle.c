@@ -1,6 +1,7 @@
 /*
  * oracle.c -- plain, slow, single-threaded FP64 reference for the sparse
- * MTTKRP / CP-ALS path.
+ * MTTKRP / CP-ALS path (plus one all-core form of the MTTKRP definition,
+ * for the timed CPU baseline).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product library calls, links or
  * includes this file; only the tests, the package smoke check and the
@@ -24,6 +25,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <fenv.h>
+#include <pthread.h>
 
 /* ---------------------------------------------------------------------- */
 /* MTTKRP, Sec. 3 eq. (mttkrp):                                            */
@@ -51,6 +53,90 @@ void oracle_mttkrp(int d, const int64_t *dims, int64_t P, const int32_t *idx,
     if (lambda)
         for (int64_t k = 0; k < In; ++k)
             for (int j = 0; j < R; ++j) V[k * ldv + j] *= lambda[j];
+}
+
+/* The same definition on T host threads (the CPU baseline's all-core form).
+ * Thread t owns the output rows [lo_t, hi_t), the ranges cut so that each
+ * holds about P / T nonzeros; it walks all nonzeros in storage order and
+ * applies those whose row it owns, exactly as oracle_mttkrp does.  Every
+ * row therefore receives the same additions in the same order as in
+ * oracle_mttkrp, and V is bit-identical to it for every T.
+ * Returns 0, or 1 if a thread or an array could not be created. */
+struct mt_job {
+    int d, n, R;
+    int64_t P, lo, hi, ldv;
+    const int32_t *idx;
+    const double *vals;
+    const double *const *A;
+    const int64_t *lda;
+    const double *lambda;
+    double *V;
+};
+
+static void *mt_worker(void *arg)
+{
+    const struct mt_job *w = (const struct mt_job *)arg;
+    for (int64_t i = 0; i < w->P; ++i) {
+        int64_t k = w->idx[(int64_t)w->n * w->P + i];
+        if (k < w->lo || k >= w->hi) continue;
+        for (int j = 0; j < w->R; ++j) {
+            double t = w->vals[i];
+            for (int m = 0; m < w->d; ++m) {
+                if (m == w->n) continue;
+                int64_t row = w->idx[(int64_t)m * w->P + i];
+                t *= w->A[m][row * w->lda[m] + j];
+            }
+            w->V[k * w->ldv + j] += t;
+        }
+    }
+    if (w->lambda)
+        for (int64_t k = w->lo; k < w->hi; ++k)
+            for (int j = 0; j < w->R; ++j) w->V[k * w->ldv + j] *= w->lambda[j];
+    return NULL;
+}
+
+int oracle_mttkrp_threads(int d, const int64_t *dims, int64_t P, const int32_t *idx,
+                          const double *vals, int n, int R, const double *const *A,
+                          const int64_t *lda, const double *lambda, double *V, int64_t ldv,
+                          int T)
+{
+    int64_t In = dims[n];
+    if (T < 1) T = 1;
+    memset(V, 0, sizeof(double) * (size_t)In * (size_t)ldv);
+    int64_t *cnt = (int64_t *)calloc((size_t)In + 1, sizeof(int64_t));
+    struct mt_job *jobs = (struct mt_job *)calloc((size_t)T, sizeof(struct mt_job));
+    pthread_t *tid = (pthread_t *)calloc((size_t)T, sizeof(pthread_t));
+    int *started = (int *)calloc((size_t)T, sizeof(int));
+    int status = (cnt && jobs && tid && started) ? 0 : 1;
+    if (!status) {
+        for (int64_t i = 0; i < P; ++i) cnt[idx[(int64_t)n * P + i]] += 1;
+        /* row ranges: thread t starts at the first row whose nonzeros before
+         * it number at least t P / T */
+        int64_t k = 0, before = 0;
+        for (int t = 0; t < T; ++t) {
+            int64_t target = P * t / T;
+            while (k < In && before < target) before += cnt[k++];
+            jobs[t].lo = (t == 0) ? 0 : k;
+        }
+        for (int t = 0; t < T; ++t) {
+            struct mt_job *w = &jobs[t];
+            w->hi = (t + 1 < T) ? jobs[t + 1].lo : In;
+            w->d = d; w->n = n; w->R = R; w->P = P; w->ldv = ldv;
+            w->idx = idx; w->vals = vals; w->A = A; w->lda = lda; w->lambda = lambda; w->V = V;
+        }
+        for (int t = 0; t < T; ++t) {
+            if (jobs[t].lo >= jobs[t].hi) continue;
+            if (pthread_create(&tid[t], NULL, mt_worker, &jobs[t]) != 0) { status = 1; break; }
+            started[t] = 1;
+        }
+        for (int t = 0; t < T; ++t)
+            if (started[t]) pthread_join(tid[t], NULL);
+    }
+    free(cnt);
+    free(jobs);
+    free(tid);
+    free(started);
+    return status;
 }
 
 /* The same definition restricted to a list of output rows: Vrows[r*ldv + j]

@@ -141,6 +141,40 @@ def test_mttkrp_rows_matches_full():
                                       full[r])
 
 
+@pytest.mark.parametrize("T", [1, 3, 8, 64])
+def test_mttkrp_threads_matches_dense_unfolding(T):
+    """The all-core form against the dense X_(n) (Khatri-Rao) product, and
+    bit for bit against the serial definition (each row gets the same adds in
+    the same order); T = 64 exceeds the rows and nonzeros of the second case,
+    a hot row takes most nonzeros of the third."""
+    dims = (9, 7, 5)
+    R = 4
+    idx, vals = synth.coo_uniform(dims, 150, 33)
+    facs = [f[:, :R].astype(np.float64) for f in synth.factor_matrices(dims, R, 33, "normal")]
+    X = _dense(idx, vals, dims)
+    lam = np.linspace(0.5, 1.5, R)
+    for n in range(3):
+        got = oracle.mttkrp_threads(idx, vals, dims, facs, n, R, T, lam=lam)
+        ref = _khatri_rao_unfold_mttkrp(X, facs, n, R) * lam
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+        np.testing.assert_array_equal(got, oracle.mttkrp(idx, vals, dims, facs, n, R, lam=lam))
+    dims = (6, 5, 4, 3)
+    idx, vals, F = synth.small_integer_case(dims, 40, 3, 12)
+    F = [f[:, :3].astype(np.float64) for f in F]
+    for n in range(4):
+        np.testing.assert_array_equal(oracle.mttkrp_threads(idx, vals, dims, F, n, 3, T),
+                                      oracle.mttkrp(idx, vals, dims, F, n, 3))
+    dims = (40, 30, 20)
+    idx, vals = synth.coo_zipf(dims, 5000, (2.5, 1.0, 0.0), 13)
+    facs = [f[:, :R].astype(np.float64) for f in synth.factor_matrices(dims, R, 13, "normal")]
+    for n in range(3):
+        np.testing.assert_array_equal(oracle.mttkrp_threads(idx, vals, dims, facs, n, R, T),
+                                      oracle.mttkrp(idx, vals, dims, facs, n, R))
+    empty = oracle.mttkrp_threads(np.zeros((3, 0), np.int32), np.zeros(0), (4, 3, 2),
+                                  [np.ones((I, 2)) for I in (4, 3, 2)], 0, 2, T)
+    assert empty.shape == (4, 2) and not empty.any()
+
+
 def test_stable_argsort_brute_force():
     rng = np.random.default_rng(3)
     for P, K in [(0, 3), (1, 1), (50, 3), (500, 40), (2000, 2000)]:
