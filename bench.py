@@ -364,22 +364,28 @@ def run_ours(args):
     achieved = (alg / d) / (launch_ms / 1e3) / 1e9
     comp_gbs = (comp / d) / (launch_ms / 1e3) / 1e9
 
-    # end to end through the public API: the factors H2D from pinned host
-    # memory, every mode's MTTKRP, every output D2H, each step
-    pin_f = [torch.from_numpy(f.view(np.int16) if dtype != "f32" else f).pin_memory() for f in facs_np]
+    # end to end through the public API: one mttkrp_from_host call per step
+    # uploads the factors from pinned host memory, runs every mode's MTTKRP
+    # (the timed region's schedules, recorded on the tensor) and downloads
+    # every output, the copies overlapped with the kernels; the step ends
+    # with the stream synchronised and the results in host memory
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtype]
+    pin_f = [torch.from_numpy(f.view(np.int16) if dtype != "f32" else f).view(tdt).pin_memory()
+             for f in facs_np]
     pin_o = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
     h2d = sum(p.numel() * p.element_size() for p in pin_f)
     d2h = sum(p.numel() * p.element_size() for p in pin_o)
+    for n in range(d):
+        P.tensor_set_schedule(T.handle, n, dtype, R, scheds[n])
+    ws = torch.empty(P.mttkrp_from_host_workspace_size(T.handle, list(range(d)), dtype, R, ld),
+                     dtype=torch.uint8, device="cuda")
+    T.mttkrp_from_host(list(range(d)), pin_f, R, outs=pin_o, workspace=ws)  # warm-up
     torch.cuda.synchronize()
     e0 = time.perf_counter()
     for _ in range(args.steps):
-        for f, p in zip(facs, pin_f):
-            f.view(p.dtype).copy_(p, non_blocking=True)
-        step()
-        for o, p in zip(outs, pin_o):
-            p.copy_(o, non_blocking=True)
-        torch.cuda.synchronize()
+        T.mttkrp_from_host(list(range(d)), pin_f, R, outs=pin_o, workspace=ws)
     e_s = (time.perf_counter() - e0) / args.steps
+    del ws
     e2e = {"value": units / e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     extra = {}

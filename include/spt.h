@@ -218,6 +218,38 @@ spt_status mttkrp_deterministic(spt_tensor t, int mode, const void *const *facto
                                 int rank, int ld, const void *lambda, void *out,
                                 const spt_schedule *sched, void *stream);
 
+/* Bytes of device workspace mttkrp_from_host needs for these modes (host
+ * logic): the factors the listed modes read and one output per listed mode,
+ * each 256-byte aligned. */
+spt_status mttkrp_from_host_workspace_size(spt_tensor t, int nmodes, const int *modes, spt_dtype fdt,
+                                           int rank, int ld, size_t *bytes);
+
+/* MTTKRP from host memory: copies the factors to the device, runs mttkrp()
+ * (the library's schedule) for modes[0], modes[1], ... in that order and
+ * copies each result back.  The copies run on two library-owned streams
+ * (created on first use per device, kept until exit) and are overlapped with
+ * the kernels: the factors are uploaded in the order the modes first need
+ * them (every factor but A^(modes[0]) first), each kernel waits only for
+ * the factors it reads, and each result is downloaded as soon as its kernel
+ * ends, while the next mode runs.  Stream-ordered: `stream` completes after
+ * the last download; host buffers must stay valid until then.  Pinned (page-
+ * locked) host buffers give the overlap; pageable ones work, with copies
+ * that block the calling thread.
+ *  modes     : host, nmodes distinct modes (1 <= nmodes <= order).
+ *  factors   : host array of d HOST pointers; factors[m] is A^(m), I_m x ld of
+ *              type fdt, row-major; may be NULL when no listed mode reads it.
+ *  lambda    : device weights as for mttkrp(), or NULL.
+ *  out       : host array of nmodes HOST pointers; out[q] receives the
+ *              I_{modes[q]} x ld result of mode modes[q] (float32; float64 for
+ *              SPT_F64), columns >= rank zero.
+ *  workspace : device, >= mttkrp_from_host_workspace_size() bytes, 256-byte
+ *              aligned; the call's device copies of the factors and results.
+ * Errors as for mttkrp(); SPT_EINVAL for a repeated or out-of-range mode, a
+ * NULL needed pointer, or a short or misaligned workspace. */
+spt_status mttkrp_from_host(spt_tensor t, int nmodes, const int *modes, const void *const *factors,
+                            spt_dtype fdt, int rank, int ld, const void *lambda, void *const *out,
+                            void *workspace, size_t workspace_bytes, void *stream);
+
 /* Record the schedule to use for (mode, fdt, rank) wherever no schedule is
  * passed (mttkrp with sched == NULL, cp_als_step), e.g. one chosen by
  * mttkrp_autotune or mttkrp_select.  s == NULL clears it.  The schedule is

@@ -95,6 +95,10 @@ _sig("mttkrp", _vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _vp, _vp
      C.POINTER(spt_schedule), _vp)
 _sig("mttkrp_deterministic", _vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _vp, _vp,
      C.POINTER(spt_schedule), _vp)
+_sig("mttkrp_from_host_workspace_size", _vp, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int,
+     C.POINTER(C.c_size_t))
+_sig("mttkrp_from_host", _vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _vp,
+     C.POINTER(_vp), _vp, C.c_size_t, _vp)
 _sig("mttkrp_default_schedule", _vp, C.c_int, C.c_int, C.c_int, C.POINTER(spt_schedule))
 _sig("tensor_set_schedule", _vp, C.c_int, C.c_int, C.c_int, C.POINTER(spt_schedule))
 _sig("mttkrp_paper_sizes", C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int))
@@ -106,6 +110,7 @@ _sig("spt_fma_probe", C.c_int, C.c_int64, _vp, C.POINTER(C.c_double), _vp)
 EXPORTED = ["spt_last_error", "spt_device_info", "tensor_create_coo", "tensor_destroy",
             "tensor_info", "tensor_get_coo", "tensor_norm2", "tensor_check",
             "build_mode_permutation", "tensor_get_permutation", "mttkrp", "mttkrp_deterministic",
+            "mttkrp_from_host_workspace_size", "mttkrp_from_host",
             "mttkrp_default_schedule", "tensor_set_schedule", "mttkrp_paper_sizes", "mttkrp_paper_schedule",
             "spt_stream_copy", "spt_convert_f32", "spt_fma_probe"]
 
@@ -237,6 +242,22 @@ def mttkrp_deterministic(t: int, mode: int, factor_ptrs: Sequence[Optional[int]]
                          stream: int = 0):
     _chk(_L.mttkrp_deterministic(t, mode, _ptrs(factor_ptrs), _dt(fdt), rank, ld, lambda_ptr or None,
                                  out_ptr, C.byref(sched) if sched is not None else None, stream or None))
+
+
+def mttkrp_from_host_workspace_size(t: int, modes: Sequence[int], fdt, rank: int, ld: int) -> int:
+    m = (C.c_int * len(modes))(*modes)
+    n = C.c_size_t()
+    _chk(_L.mttkrp_from_host_workspace_size(t, len(modes), m, _dt(fdt), rank, ld, C.byref(n)))
+    return n.value
+
+
+def mttkrp_from_host(t: int, modes: Sequence[int], host_factor_ptrs: Sequence[Optional[int]], fdt, rank: int,
+                     ld: int, lambda_ptr: Optional[int], host_out_ptrs: Sequence[int], ws_ptr: int,
+                     ws_bytes: int, stream: int = 0):
+    m = (C.c_int * len(modes))(*modes)
+    outs = (_vp * len(host_out_ptrs))(*[p or None for p in host_out_ptrs])
+    _chk(_L.mttkrp_from_host(t, len(modes), m, _ptrs(host_factor_ptrs), _dt(fdt), rank, ld, lambda_ptr or None,
+                             outs, ws_ptr, ws_bytes, stream or None))
 
 
 def mttkrp_default_schedule(t: int, mode: int, fdt, rank: int) -> spt_schedule:

@@ -108,6 +108,39 @@ class SparseTensor:
            lam.data_ptr() if lam is not None else 0, out.data_ptr(), sched, _stream())
         return out
 
+    def mttkrp_from_host(self, modes: Sequence[int], factors: List[Optional[torch.Tensor]], rank: int,
+                         outs: Optional[List[torch.Tensor]] = None, lam: Optional[torch.Tensor] = None,
+                         workspace: Optional[torch.Tensor] = None, sync: bool = True) -> List[torch.Tensor]:
+        """MTTKRP of `modes` from host memory (mttkrp_from_host): factors are
+        CPU torch tensors (pinned ones let the copies overlap the kernels),
+        outs CPU tensors (allocated pinned if None).  With sync=False the
+        results are valid once the current stream has completed."""
+        f0 = next(f for f in factors if f is not None)
+        ld = f0.shape[1]
+        fdt = _TORCH_DT[f0.dtype]
+        odt = torch.float64 if fdt == "f64" else torch.float32
+        if outs is None:
+            outs = [torch.empty((self.dims[n], ld), dtype=odt).pin_memory() for n in modes]
+        for m, f in enumerate(factors):  # the library copies dims[m] x ld elements
+            if f is not None and (f.is_cuda or f.dtype != f0.dtype or not f.is_contiguous()
+                                  or f.shape != (self.dims[m], ld)):
+                raise ValueError(f"factor {m}: a contiguous host tensor of shape ({self.dims[m]}, {ld}) "
+                                 f"and dtype {f0.dtype} is required")
+        for q, n in enumerate(modes):
+            o = outs[q]
+            if o.is_cuda or o.dtype != odt or not o.is_contiguous() or o.shape != (self.dims[n], ld):
+                raise ValueError(f"outs[{q}]: a contiguous host tensor of shape ({self.dims[n]}, {ld}) "
+                                 f"and dtype {odt} is required")
+        need = B.mttkrp_from_host_workspace_size(self.handle, list(modes), fdt, rank, ld)
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+        B.mttkrp_from_host(self.handle, list(modes), [f.data_ptr() if f is not None else 0 for f in factors],
+                           fdt, rank, ld, lam.data_ptr() if lam is not None else 0,
+                           [o.data_ptr() for o in outs], workspace.data_ptr(), workspace.numel(), _stream())
+        if sync:
+            torch.cuda.current_stream().synchronize()
+        return outs
+
     def gcp_gradient(self, mode: int, factors: List[torch.Tensor], rank: int, loss: str,
                      out: Optional[torch.Tensor] = None):
         """Generalised CP loss gradient with respect to factors[mode] (all d
