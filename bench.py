@@ -364,9 +364,9 @@ def run_ours(args):
     achieved = (alg / d) / (launch_ms / 1e3) / 1e9
     comp_gbs = (comp / d) / (launch_ms / 1e3) / 1e9
 
-    # the metric as the survey defines it: P R / t_mode with t_mode the median
-    # of 20 CUDA-graph replays of that mode's launch (after 3), beside the
-    # timed region's whole-step figure
+    # the metric's per-mode form: P R / t_mode with t_mode the median of 20
+    # CUDA-graph replays of that mode's launch (after 3), beside the timed
+    # region's whole-step figure
     graph_mode_ms = None
     try:
         graph_mode_ms = []

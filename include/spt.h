@@ -40,7 +40,7 @@ typedef enum {
     SPT_ERANGE = 2,       /* a coordinate outside [0, I_m) */
     SPT_ENOMEM = 3,       /* device or host allocation failed */
     SPT_ECUDA = 4,        /* a CUDA runtime call or kernel failed */
-    SPT_EUNSUPPORTED = 5, /* valid request outside what this build implements */
+    SPT_EUNSUPPORTED = 5, /* valid request outside what the library implements */
     SPT_ESINGULAR = 6,    /* normal-equation matrix not positive definite (after ridge retry) */
     SPT_ETIMEOUT = 7,     /* a bounded device-side wait ran out */
     SPT_ESTATE = 8        /* the call needs an earlier step (e.g. a coalesced tensor) */
