@@ -47,6 +47,27 @@ def test_argument_errors_without_device():
         P.tensor_create_coo(2, [4, 4], 5, [0, 0], 0)
     assert ei.value.status == P.SPT_EINVAL
     assert "NULL" in P.spt_last_error()
+    L = P.binding.lib()  # NULL tensors: refused before any device work
+    n = C.c_size_t()
+    modes = (C.c_int * 1)(0)
+    assert L.mttkrp_from_host_workspace_size(None, 1, modes, 0, 8, 8, C.byref(n)) == P.SPT_EINVAL
+    assert L.mttkrp_from_host(None, 1, modes, None, 0, 8, 8, None, None, None, 0, None) == P.SPT_EINVAL
+    assert L.mttkrp_deterministic(None, 0, None, 0, 8, 8, None, None, None, None) == P.SPT_EINVAL
+    assert L.gcp_gradient(None, 0, None, 0, 8, 8, 0, None, None, None) == P.SPT_EINVAL
+
+
+def test_product_path_never_uses_the_oracle():
+    """The package and the CUDA sources neither import, include nor load
+    anything under oracle/ (the oracle is test infrastructure only)."""
+    pkg = os.path.join(ROOT, "paper_1809_09175_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if not fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                continue
+            src = open(os.path.join(dirpath, fn)).read()
+            assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), fn
+            assert "liboracle" not in src and "oracle.c" not in src and "oracle/" not in src, fn
+            assert not re.search(r'#include\s+"[^"]*oracle', src), fn
 
 
 def test_paper_sizes_table_matches_golden():
