@@ -134,3 +134,47 @@ def test_gcp_pin_rejects_planted_mistake(name):
                 if abs(F - Fd) > 1e-10 * max(1.0, abs(Fd)) or np.abs(G - fd).max() > 1e-6 * max(1.0, np.abs(fd).max()):
                     caught = True
     assert caught, f"planted mistake {name} passed the generalised CP pin"
+
+
+# planted mistakes in the all-core form, caught by its pins (dense unfolding,
+# bit-identical to the serial definition)
+THREAD_MUTATIONS = {
+    "boundary_row_twice": ("if (k < w->lo || k >= w->hi) continue;", "if (k < w->lo || k > w->hi) continue;"),
+    "overwrite_not_accumulate": ("w->V[k * w->ldv + j] += t;", "w->V[k * w->ldv + j] = t;"),
+    "last_row_dropped": ("w->hi = (t + 1 < T) ? jobs[t + 1].lo : In;", "w->hi = (t + 1 < T) ? jobs[t + 1].lo : In - 1;"),
+    "lambda_twice": ("        for (int64_t k = w->lo; k < w->hi; ++k)\n            for (int j = 0; j < w->R; ++j) w->V[k * w->ldv + j] *= w->lambda[j];",
+                     "        for (int64_t k = w->lo; k < w->hi; ++k)\n            for (int j = 0; j < w->R; ++j) w->V[k * w->ldv + j] *= w->lambda[j] * w->lambda[j];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(THREAD_MUTATIONS))
+def test_thread_pins_reject_planted_mistake(name):
+    dims = (9, 7, 5)
+    R = 4
+    idx, vals = synth.coo_uniform(dims, 150, 33)
+    facs = [f[:, :R].astype(np.float64) for f in synth.factor_matrices(dims, R, 33, "normal")]
+    lam = np.array([0.5, 1.5, 2.0, 0.75])
+    X = _dense(idx, vals, dims)
+    dp = C.POINTER(C.c_double)
+    fs = [np.ascontiguousarray(f) for f in facs]
+    arr = (dp * 3)(*[f.ctypes.data_as(dp) for f in fs])
+    lda = np.array([R] * 3, dtype=np.int64)
+    dims_a = np.array(dims, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    v64 = np.ascontiguousarray(vals, dtype=np.float64)
+    caught = False
+    with tempfile.TemporaryDirectory() as tmp:
+        L = _build_variant(name, *THREAD_MUTATIONS[name], tmp)
+        L.oracle_mttkrp_threads.argtypes = [C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int,
+                                            C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                            C.c_int]
+        for T in (3, 8):
+            for n in range(3):
+                V = np.zeros((dims[n], R))
+                L.oracle_mttkrp_threads(3, dims_a.ctypes.data, idx.shape[1], idx.ctypes.data, v64.ctypes.data, n,
+                                        R, C.cast(arr, C.c_void_p), lda.ctypes.data, lam.ctypes.data,
+                                        V.ctypes.data, R, T)
+                ref = _khatri_rao_unfold_mttkrp(X, facs, n, R) * lam[None, :]
+                if not np.allclose(V, ref, rtol=1e-12, atol=1e-12):
+                    caught = True
+    assert caught, f"planted mistake {name} passed the all-core pins"
