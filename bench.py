@@ -47,7 +47,7 @@ def parse():
                          "or its default rule")
     ap.add_argument("--npg", type=int, default=0, help="override the schedule's nonzeros per lane group")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (debug only)")
-    ap.add_argument("--cpu-sample", type=int, default=4_000_000,
+    ap.add_argument("--cpu-sample", type=int, default=32_000_000,
                     help="nonzeros of the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the variants / CP-ALS extras")
