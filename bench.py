@@ -421,7 +421,6 @@ def run_ours(args):
             extra = measure_extras(args, P, torch, w, T, idx, vals, facs_np, dtype, R, d, ld, outs,
                                    sched_for, mode_ms)
         except Exception as ex:  # the headline above stands; say what the extras hit
-            torch.cuda.synchronize()
             extra = {"extras_error": f"{type(ex).__name__}: {ex}"[:300]}
     if rank != 0:
         T.close()
