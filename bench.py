@@ -433,7 +433,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if dtype == "f64" else "f32",  # accumulation; 16-bit factors widen to fp32
         "data": "synthetic",
         "config": {"workload": w.name, "dims": w.dims, "nnz": w.nnz, "zipf_s": w.s, "R": R,
                    "factors": dtype, "factor_dist": w.factor_dist, "scatter": args.scatter,
