@@ -394,26 +394,30 @@ def run_ours(args):
     # (the timed region's schedules, recorded on the tensor) and downloads
     # every output, the copies overlapped with the kernels; the step ends
     # with the stream synchronised and the results in host memory
-    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtype]
-    pin_f = [torch.from_numpy(f.view(np.int16) if dtype != "f32" else f).view(tdt).pin_memory()
-             for f in facs_np]
-    pin_o = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
-    h2d = sum(p.numel() * p.element_size() for p in pin_f)
-    d2h = sum(p.numel() * p.element_size() for p in pin_o)
-    for n in range(d):
-        P.tensor_set_schedule(T.handle, n, dtype, R, scheds[n])
-    ws = torch.empty(P.mttkrp_from_host_workspace_size(T.handle, list(range(d)), dtype, R, ld),
-                     dtype=torch.uint8, device="cuda")
-    T.mttkrp_from_host(list(range(d)), pin_f, R, outs=pin_o, workspace=ws)  # warm-up
-    torch.cuda.synchronize()
-    e0 = time.perf_counter()
-    for _ in range(args.steps):
-        T.mttkrp_from_host(list(range(d)), pin_f, R, outs=pin_o, workspace=ws)
-    e_s = (time.perf_counter() - e0) / args.steps
-    del ws
-    for n in range(d):  # the variants below pass their own schedules or take the default rule
-        P.tensor_set_schedule(T.handle, n, dtype, R, None)
-    e2e = {"value": units / e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    try:
+        tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtype]
+        pin_f = [torch.from_numpy(f.view(np.int16) if dtype != "f32" else f).view(tdt).pin_memory()
+                 for f in facs_np]
+        pin_o = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+        h2d = sum(p.numel() * p.element_size() for p in pin_f)
+        d2h = sum(p.numel() * p.element_size() for p in pin_o)
+        for n in range(d):
+            P.tensor_set_schedule(T.handle, n, dtype, R, scheds[n])
+        ws = torch.empty(P.mttkrp_from_host_workspace_size(T.handle, list(range(d)), dtype, R, ld),
+                         dtype=torch.uint8, device="cuda")
+        T.mttkrp_from_host(list(range(d)), pin_f, R, outs=pin_o, workspace=ws)  # warm-up
+        torch.cuda.synchronize()
+        e0 = time.perf_counter()
+        for _ in range(args.steps):
+            T.mttkrp_from_host(list(range(d)), pin_f, R, outs=pin_o, workspace=ws)
+        e_s = (time.perf_counter() - e0) / args.steps
+        del ws
+        for n in range(d):  # the variants below pass their own schedules or take the default rule
+            P.tensor_set_schedule(T.handle, n, dtype, R, None)
+        e2e = {"value": units / e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    except P.SptError as ex:  # reported, never fatal: the device-timed line stands
+        e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+               "error": str(ex)[:300]}
 
     extra = {}
     if rank == 0 and not args.quick:
