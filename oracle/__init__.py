@@ -47,6 +47,7 @@ def lib():
         L.oracle_cp_als_iter.argtypes = [C.c_int, _lp, C.c_int64, _ip, _dp, C.c_int,
                                          C.POINTER(_dp), _dp, C.c_int, C.c_double, _dp]
         L.oracle_cp_als_iter.restype = C.c_int
+        L.oracle_round_bf16.argtypes = [C.c_int64, _dp, _dp]
         L.oracle_gcp_grad.argtypes = [C.c_int, _lp, C.c_int64, _ip, _dp, C.c_int, C.c_int,
                                       C.POINTER(_dp), _lp, C.c_int, _dp, C.c_int64]
         L.oracle_gcp_grad.restype = C.c_double
@@ -109,9 +110,12 @@ def mttkrp(idx, vals, dims, factors, n: int, R: int, lam=None, ld: Optional[int]
 
 def mttkrp_threads(idx, vals, dims, factors, n: int, R: int, threads: int, lam=None,
                    ld: Optional[int] = None):
-    """The MTTKRP definition on ``threads`` host threads: contiguous nonzero
-    ranges into private arrays, added in thread order (the CPU baseline's
-    all-core form; ``threads=1`` is ``mttkrp`` operation for operation)."""
+    """The MTTKRP definition on ``threads`` host threads (the CPU baseline's
+    all-core form).  Thread t owns a contiguous range of output rows, cut so
+    that each range holds about P/threads nonzeros; every thread walks all
+    nonzeros in storage order and applies only those of its own rows, so each
+    row receives its additions in the serial order and the result is
+    bit-identical to ``mttkrp`` for any thread count."""
     idx, vals = _prep(idx, vals)
     d, P = idx.shape
     dims_a = np.array(dims, dtype=np.int64)
@@ -212,6 +216,16 @@ def cp_als_iter(idx, vals, dims, factors: List[np.ndarray], R: int, bf16: bool =
     st = lib().oracle_cp_als_iter(d, _l(dims_a), P, _i(idx), _d(vals), R, arr, _d(lam),
                                   int(bf16), x2, _d(fit))
     return lam, float(fit[0]), int(st)
+
+
+def round_bf16(x) -> np.ndarray:
+    """Each float64 value rounded to the nearest bfloat16 value (ties to
+    even, bfloat16 subnormals, overflow to infinity); returned as float64.
+    The rounding the bf16 CP-ALS oracle applies to updated factors."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    lib().oracle_round_bf16(x.size, _d(x), _d(y))
+    return y
 
 
 def mlp_forward(X, params):

@@ -288,14 +288,34 @@ int oracle_cholesky(int R, const double *H, double *L)
     return 0;
 }
 
-/* Round to the nearest bf16 value (8 significant bits), ties to even. */
+/* Round a double to the nearest bfloat16 value, ties to even.  bfloat16 is
+ * the upper half of an IEEE binary32: 8 exponent bits (bias 127) and 8
+ * significant bits (7 stored), so
+ *   normal numbers, |x| >= 2^-126 : 8 significant bits;
+ *   subnormals,     |x| <  2^-126 : multiples of 2^-133 (the spacing of
+ *                                   the smallest normal binade);
+ *   the largest finite value is (2 - 2^-7) * 2^127; anything that rounds
+ *   past it becomes +-infinity.
+ * The value is scaled by a power of two (exact) so that the kept bits are
+ * its integer part, rounded with nearbyint (the default rounding mode,
+ * nearest-even), and scaled back. */
 static double round_bf16(double x)
 {
     if (x == 0.0 || !isfinite(x)) return x;
     int e;
-    double m = frexp(x, &e);          /* x = m * 2^e, 0.5 <= |m| < 1 */
-    double q = nearbyint(m * 256.0);  /* default rounding mode: nearest-even */
-    return ldexp(q, e - 8);
+    double m = frexp(x, &e);               /* x = m * 2^e, 0.5 <= |m| < 1 */
+    int bits = e - 1 >= -126 ? 8 : e + 133; /* significant bits kept: x's leading
+                                              bit is 2^(e-1), the last kept 2^-133 */
+    double q = nearbyint(ldexp(m, bits));  /* bits <= 0: |m 2^bits| <= 1/2 -> 0 */
+    double r = ldexp(q, e - bits);
+    if (fabs(r) > ldexp(255.0, 120)) return copysign(INFINITY, x);
+    return r;
+}
+
+/* Elementwise round_bf16 (exported so the rounding can be checked alone). */
+void oracle_round_bf16(int64_t n, const double *x, double *y)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = round_bf16(x[i]);
 }
 
 /* One CP-ALS iteration (all modes in order 0..d-1), in place.

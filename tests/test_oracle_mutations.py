@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import synth
-from tests.test_oracle_pins import _dense, _khatri_rao_unfold_mttkrp
+from tests.test_oracle_pins import _bf16_pin_values, _dense, _khatri_rao_unfold_mttkrp, _ref_bf16
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "oracle.c")
 
@@ -178,3 +178,26 @@ def test_thread_pins_reject_planted_mistake(name):
                 if not np.allclose(V, ref, rtol=1e-12, atol=1e-12):
                     caught = True
     assert caught, f"planted mistake {name} passed the all-core pins"
+
+
+# Plausible mistakes in the oracle's bf16 rounding (the step the bf16 CP-ALS
+# oracle applies to each updated factor); the bit-level pin must reject each.
+ROUND_MUTATIONS = {
+    "truncation": ("double q = nearbyint(ldexp(m, bits));", "double q = trunc(ldexp(m, bits));"),
+    "ties_away_from_zero": ("double q = nearbyint(ldexp(m, bits));", "double q = round(ldexp(m, bits));"),
+    "no_subnormal_range": ("int bits = e - 1 >= -126 ? 8 : e + 133;", "int bits = 8;"),
+    "no_overflow": ("if (fabs(r) > ldexp(255.0, 120)) return copysign(INFINITY, x);", ""),
+    "seven_bits": ("int bits = e - 1 >= -126 ? 8 : e + 133;", "int bits = e - 1 >= -126 ? 7 : e + 132;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ROUND_MUTATIONS))
+def test_bf16_pin_rejects_planted_rounding_mistake(name):
+    x = _bf16_pin_values()
+    ref = np.array([_ref_bf16(float(t)) for t in x])
+    with tempfile.TemporaryDirectory() as tmp:
+        L = _build_variant("round_" + name, *ROUND_MUTATIONS[name], tmp)
+        L.oracle_round_bf16.argtypes = [C.c_int64, C.c_void_p, C.c_void_p]
+        y = np.empty_like(x)
+        L.oracle_round_bf16(x.size, x.ctypes.data, y.ctypes.data)
+    assert (y.view(np.uint64) != ref.view(np.uint64)).any(), f"planted mistake {name} passed the bf16 pin"

@@ -6,6 +6,8 @@ arithmetic, invariants, brute force on tiny inputs, or recovery of a known
 CP model.  None of them re-types the oracle's own loop.
 """
 import itertools
+import math
+import struct
 
 import numpy as np
 import pytest
@@ -276,6 +278,77 @@ def test_cp_als_fit_and_normal_equations():
     V = oracle.mttkrp(idx, v64, dims, A, 2, R)
     H = (A[0].T @ A[0]) * (A[1].T @ A[1])
     np.testing.assert_allclose(V, (A[2] * lam[None, :]) @ H, rtol=1e-9, atol=1e-10)
+
+
+def _ref_bf16(x: float) -> float:
+    """bfloat16 round-to-nearest-even written on the IEEE bit fields of a
+    double: keep the top k bits of the 53-bit integer significand M (k = 8 for
+    normal bfloat16 results, fewer below 2^-126 where the spacing stays
+    2^-133), add one to the kept part when the dropped bits exceed half of its
+    last place, or equal half and the kept part is odd; overflow past the
+    largest finite bfloat16, 0x7f7f = 255 * 2^120, gives infinity."""
+    if x == 0.0 or not math.isfinite(x):
+        return x
+    bits = struct.unpack("<Q", struct.pack("<d", x))[0]
+    sign = -1.0 if bits >> 63 else 1.0
+    ef = (bits >> 52) & 0x7FF
+    if ef == 0:  # a double subnormal: far below half the smallest bfloat16
+        return sign * 0.0
+    E = ef - 1023
+    M = (bits & ((1 << 52) - 1)) | (1 << 52)
+    k = 8 if E >= -126 else E + 134
+    if k < 0:
+        return sign * 0.0
+    drop = 53 - k
+    q, rem, half = M >> drop, M & ((1 << drop) - 1), 1 << (drop - 1)
+    if rem > half or (rem == half and (q & 1)):
+        q += 1
+    r = math.ldexp(q, E - 52 + drop)
+    if r > 255.0 * 2.0 ** 120:
+        return sign * math.inf
+    return sign * r
+
+
+def _bf16_pin_values() -> np.ndarray:
+    """Exact ties (even and odd kept parts) in several binades, their
+    neighbours one double ulp away, bfloat16 subnormals with their ties, the
+    underflow and overflow thresholds, signed zeros and random values."""
+    v = []
+    for e in (-100, -20, -1, 0, 3, 60, 127):
+        for j in range(128):
+            base = 1.0 + j * 2.0 ** -7
+            tie = math.ldexp(base + 2.0 ** -8, e)
+            v += [math.ldexp(base, e), tie, np.nextafter(tie, np.inf), np.nextafter(tie, -np.inf)]
+    for j in range(0, 128):  # subnormal bfloat16: multiples of 2^-133
+        tie = (j + 0.5) * 2.0 ** -133
+        v += [j * 2.0 ** -133, tie, np.nextafter(tie, np.inf), np.nextafter(tie, -np.inf)]
+    v += [2.0 ** -126, np.nextafter(2.0 ** -126, 0.0), 2.0 ** -134, 2.0 ** -134 * (1 + 2.0 ** -20),
+          2.0 ** -135, 5e-324, 255.0 * 2.0 ** 120, 255.5 * 2.0 ** 120,
+          np.nextafter(255.5 * 2.0 ** 120, 0.0), 2.0 ** 128, 1e300, 0.0, -0.0]
+    rng = np.random.default_rng(7)
+    v += list(rng.uniform(0.0, 1.0, 3000))
+    v += list(np.exp(rng.uniform(-300.0, 90.0, 3000)) * rng.choice([-1.0, 1.0], 3000))
+    a = np.array(v, dtype=np.float64)
+    return np.concatenate([a, -a])
+
+
+def test_round_bf16_is_bitwise_round_to_nearest_even():
+    x = _bf16_pin_values()
+    got = oracle.round_bf16(x)
+    ref = np.array([_ref_bf16(float(t)) for t in x])
+    bad = np.nonzero(got.view(np.uint64) != ref.view(np.uint64))[0]
+    assert bad.size == 0, [(x[i], got[i], ref[i]) for i in bad[:5]]
+
+
+def test_round_bf16_agrees_with_torch_on_float32_inputs():
+    # torch's CPU float32 -> bfloat16 conversion (round to nearest even) on
+    # values that are exactly float32, including float32 subnormals
+    import torch
+    v = _bf16_pin_values()
+    x = v[np.abs(v) < 3.0e38].astype(np.float32).astype(np.float64)
+    got = oracle.round_bf16(x)
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(got.view(np.uint64), ref.view(np.uint64))
 
 
 def test_cp_als_bf16_rounding_keeps_values_on_bf16_grid():
