@@ -394,6 +394,7 @@ def run_ours(args):
     # (the timed region's schedules, recorded on the tensor) and downloads
     # every output, the copies overlapped with the kernels; the step ends
     # with the stream synchronised and the results in host memory
+    ws = None
     try:
         tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtype]
         pin_f = [torch.from_numpy(f.view(np.int16) if dtype != "f32" else f).view(tdt).pin_memory()
@@ -411,13 +412,17 @@ def run_ours(args):
         for _ in range(args.steps):
             T.mttkrp_from_host(list(range(d)), pin_f, R, outs=pin_o, workspace=ws)
         e_s = (time.perf_counter() - e0) / args.steps
-        del ws
-        for n in range(d):  # the variants below pass their own schedules or take the default rule
-            P.tensor_set_schedule(T.handle, n, dtype, R, None)
         e2e = {"value": units / e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
     except P.SptError as ex:  # reported, never fatal: the device-timed line stands
         e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
                "error": str(ex)[:300]}
+    finally:
+        # a failed call still orders the stream after its queued copies: wait
+        # for them before the workspace goes back to torch's allocator
+        torch.cuda.current_stream().synchronize()
+        del ws
+        for n in range(d):  # the variants below pass their own schedules or take the default rule
+            P.tensor_set_schedule(T.handle, n, dtype, R, None)
 
     extra = {}
     if rank == 0 and not args.quick:

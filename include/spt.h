@@ -134,7 +134,9 @@ spt_status tensor_get_coo(spt_tensor t, int32_t *const *idx, float *vals, void *
 spt_status tensor_norm2(spt_tensor t, double *out);
 
 /* Synchronise `stream` and read the tensor's device status word: SPT_OK, or
- * SPT_ETIMEOUT if a kernel's bounded wait ran out since the tensor was made. */
+ * SPT_ETIMEOUT if a kernel's bounded wait ran out since the tensor was made
+ * or since the last tensor_check that reported it (a reported status is
+ * cleared, so later calls start clean). */
 spt_status tensor_check(spt_tensor t, void *stream);
 
 /* ---- mode permutations (Sec. 6) --------------------------------------- */
@@ -172,8 +174,10 @@ spt_status tensor_get_permutation(spt_tensor t, int mode, int32_t *perm, void *s
  *           keys in position order (the same result as perm_n).
  * The sort works in one static device array that is part of the library and
  * stays allocated on every GPU that has loaded it until the process exits.
- * The first call on each device looks up that array's device address (with
- * the device current), so make that first call before any stream capture.
+ * Every call looks up that array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing); the first lookup on a
+ * device also loads the library's device code there, so make the first call
+ * on each device before any stream capture.
  * Every call uses the same array and leaves its last contents there; calls
  * that overlap on the GPU (other streams or host threads) race on it, so the
  * caller must order them.  Nothing is allocated or freed. */
@@ -232,7 +236,9 @@ spt_status mttkrp_from_host_workspace_size(spt_tensor t, int nmodes, const int *
  * them (every factor but A^(modes[0]) first), each kernel waits only for
  * the factors it reads, and each result is downloaded as soon as its kernel
  * ends, while the next mode runs.  Stream-ordered: `stream` completes after
- * the last download; host buffers must stay valid until then.  Pinned (page-
+ * the last download; host buffers must stay valid until then.  A call that
+ * fails after queuing copies still orders `stream` after them, so the
+ * workspace and host buffers may be released once `stream` is done.  Pinned (page-
  * locked) host buffers give the overlap; pageable ones work, with copies
  * that block the calling thread.
  *  modes     : host, nmodes distinct modes (1 <= nmodes <= order).
@@ -394,7 +400,7 @@ spt_status mttkrp_batch_run(spt_batch b, void *stream);
 spt_status mttkrp_batch_info(spt_batch b, int64_t *tasks, int64_t *items, int *blocks);
 
 /* Synchronise `stream` and read the batch kernel's status word (SPT_ETIMEOUT
- * if a bounded wait ran out). */
+ * if a bounded wait ran out); a reported status is cleared. */
 spt_status mttkrp_batch_check(spt_batch b, void *stream);
 
 /* Free a batch (synchronises the device). */
@@ -475,6 +481,19 @@ spt_status spt_fma_probe(spt_dtype dt, int64_t iters, double *sink, double *flop
 
 /* Convert n float32 values to fdt storage (round to nearest even). */
 spt_status spt_convert_f32(const float *src, void *dst, spt_dtype fdt, int64_t n, void *stream);
+
+/* Try budget of the bounded waits in the MTTKRP kernels (the staging
+ * barriers of the bulk copies; failure detection, no counterpart in the
+ * paper).  A wait that runs out of tries sets the tensor's (or batch's)
+ * status word, lets the warp's copies in flight land (with the full default
+ * budget), and ends the warp's work; tensor_check / mttkrp_batch_check then
+ * report SPT_ETIMEOUT.  Applies to launches made after the call, library-wide
+ * (captured CUDA graphs and batch tables keep the budget they were made with).
+ *  tries : -1 restores the default (2^22 tries of about 1 us each); 0 makes
+ *          every such wait give up at once, which is how the timeout path is
+ *          tested without a fault; otherwise the number of try_wait calls.
+ * SPT_EINVAL for tries < -1 or >= 2^32.  Host logic, no launch. */
+spt_status spt_set_wait_tries(int64_t tries);
 
 /* Number of SMs of the current device and this library's build arch (e.g. 103). */
 spt_status spt_device_info(int *sm_count, int *arch);

@@ -156,6 +156,7 @@ _try_sig("mttkrp_batch_run", _vp, _vp)
 _try_sig("mttkrp_batch_info", _vp, _i64p, _i64p, C.POINTER(C.c_int))
 _try_sig("mttkrp_batch_check", _vp, _vp)
 _try_sig("mttkrp_batch_destroy", _vp)
+_try_sig("spt_set_wait_tries", C.c_int64)
 SPT_NOALLOC_MAX_NNZ = 1835008
 
 
@@ -312,6 +313,11 @@ def cp_als_step(t: int, factor_ptrs: Sequence[int], fdt, rank: int, ld: int, lam
 
 def cp_als_status(workspace_ptr: int, stream: int = 0):
     _chk(_L.cp_als_status(workspace_ptr, stream or None))
+
+
+def spt_set_wait_tries(tries: int):
+    """Try budget of the kernels' bounded waits for later launches (-1 = default)."""
+    _chk(_L.spt_set_wait_tries(int(tries)))
 
 
 def mode_permutation_noalloc(keys_ptr: int, n: int, dim: int, perm_ptr: int, stream: int = 0):

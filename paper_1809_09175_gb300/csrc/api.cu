@@ -232,6 +232,10 @@ spt_status tensor_check(spt_tensor t, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     SPT_CUDA(cudaMemcpyAsync(&h, t->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     SPT_CUDA(cudaStreamSynchronize(st));
+    if (h) {  // reported once: clear the word for the calls that follow
+        SPT_CUDA(cudaMemsetAsync(t->dev_err, 0, sizeof(int), st));
+        SPT_CUDA(cudaStreamSynchronize(st));
+    }
     if (h == SPT_DEV_TIMEOUT) return fail(SPT_ETIMEOUT, "a bounded device wait ran out");
     if (h) return fail(SPT_ECUDA, "device status word " + std::to_string(h));
     return SPT_OK;

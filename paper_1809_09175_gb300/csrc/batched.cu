@@ -269,7 +269,10 @@ spt_status mttkrp_batch_create(int count, const spt_batch_item *items, spt_dtype
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, b->wpc * 32, k.smem);
         if (e == cudaSuccess && bps < 1) { free_batch(b); return fail(SPT_EINVAL, "batch kernel does not fit"); }
         k.blocks = bps * sm_count();
-        for (auto &tk : k.htasks) tk.p.err = b->err;
+        for (auto &tk : k.htasks) {
+            tk.p.err = b->err;
+            tk.p.wait_tries = wait_tries();
+        }
         if (e == cudaSuccess) e = cudaMalloc(&k.dtasks, sizeof(BatchTask) * std::max<size_t>(1, k.htasks.size()));
         if (e == cudaSuccess)
             e = cudaMemcpy(k.dtasks, k.htasks.data(), sizeof(BatchTask) * k.htasks.size(), cudaMemcpyHostToDevice);
@@ -318,7 +321,12 @@ spt_status mttkrp_batch_check(spt_batch b, void *stream) {
     int h = 0;
     SPT_CUDA(cudaMemcpyAsync(&h, b->err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     SPT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (h) {  // reported once: clear the word for the runs that follow
+        SPT_CUDA(cudaMemsetAsync(b->err, 0, sizeof(int), (cudaStream_t)stream));
+        SPT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    }
     if (h == SPT_DEV_TIMEOUT) return fail(SPT_ETIMEOUT, "a bounded device wait ran out");
+    if (h) return fail(SPT_ECUDA, "device status word " + std::to_string(h));
     return SPT_OK;
 }
 

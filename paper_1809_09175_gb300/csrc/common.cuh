@@ -155,11 +155,12 @@ __device__ __forceinline__ void red_add_cluster(uint32_t addr, double v) {
     asm volatile("red.relaxed.cluster.shared::cluster.add.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
 }
 
-// Bounded wait for phase `parity` of `bar`.  Returns true when the phase
-// completed, false when the try budget ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait for phase `parity` of `bar`: at most `tries` try_wait calls.
+// Returns true when the phase completed, false when the budget ran out
+// (tries = 0 gives up at once without looking).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t tries = SPT_WAIT_TRIES) {
     uint32_t addr = smem_u32(bar);
-    for (uint32_t it = 0; it < SPT_WAIT_TRIES; ++it) {
+    for (uint32_t it = 0; it < tries; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

@@ -134,10 +134,12 @@ spt_status mttkrp_from_host(spt_tensor t, int nmodes, const int *modes, const vo
     cudaEvent_t e_start = nullptr, e_up[SPT_MAX_ORDER] = {nullptr}, e_done = nullptr;
     const void *dfac[SPT_MAX_ORDER] = {nullptr};
     bool waited[SPT_MAX_ORDER] = {false};
+    bool on_copy_streams = false;  // work may have been queued on cs->up / cs->down
     do {
         // the workspace is free once the caller's earlier work on `stream` is done
         if ((e = new_event(e_start)) != cudaSuccess) break;
         if ((e = cudaEventRecord(e_start, st)) != cudaSuccess) break;
+        on_copy_streams = true;
         if ((e = cudaStreamWaitEvent(cs->up, e_start, 0)) != cudaSuccess) break;
         if ((e = cudaStreamWaitEvent(cs->down, e_start, 0)) != cudaSuccess) break;
         for (int k = 0; k < pl.nfac && e == cudaSuccess; ++k) {
@@ -173,6 +175,19 @@ spt_status mttkrp_from_host(spt_tensor t, int nmodes, const int *modes, const vo
         if ((e = cudaEventRecord(e_done, cs->down)) != cudaSuccess) break;
         e = cudaStreamWaitEvent(st, e_done, 0);
     } while (false);
+    if ((c || e != cudaSuccess) && on_copy_streams) {
+        // a failed call still leaves `stream` ordered after every copy it
+        // queued, so the caller may free or reuse the workspace and the host
+        // buffers once `stream` is done; if the join cannot be enqueued, wait
+        // for the copy streams here
+        for (cudaStream_t cst : {cs->up, cs->down}) {
+            cudaEvent_t j = nullptr;
+            bool joined = cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess &&
+                          cudaEventRecord(j, cst) == cudaSuccess && cudaStreamWaitEvent(st, j, 0) == cudaSuccess;
+            if (j) cudaEventDestroy(j);
+            if (!joined) cudaStreamSynchronize(cst);
+        }
+    }
     for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);  // released once their work completes
     if (c) return c;
     if (e != cudaSuccess) return cuda_fail(e, "mttkrp_from_host");

@@ -49,6 +49,9 @@ int private_cluster_log2(int64_t In, int rank, size_t warp_smem, int ab);
 // on (tensor, mode) with factors of type fdt.
 spt_schedule candidate(int q, int rank);
 bool candidate_valid(spt_tensor t, int mode, int rank, spt_dtype fdt, const spt_schedule &s, int q);
+// Try budget of the kernels' staging waits for launches made from now on
+// (spt_set_wait_tries; SPT_WAIT_TRIES by default).
+uint32_t wait_tries();
 // forget the CUDA graphs captured for a tensor (its buffers changed or it died)
 void drop_graphs(spt_tensor t);
 

@@ -1,4 +1,5 @@
 // mttkrp_host.cu -- schedule logic and launch of the MTTKRP kernel.
+#include <atomic>
 #include <mutex>
 #include <unordered_map>
 
@@ -11,6 +12,11 @@
 #endif
 
 namespace spt {
+
+namespace {
+std::atomic<uint32_t> g_wait_tries{SPT_WAIT_TRIES};
+}
+uint32_t wait_tries() { return g_wait_tries.load(std::memory_order_relaxed); }
 
 int elem_bytes(spt_dtype fdt) { return fdt == SPT_F64 ? 8 : (fdt == SPT_F32 ? 4 : 2); }
 int acc_bytes(spt_dtype fdt) { return fdt == SPT_F64 ? 8 : 4; }
@@ -257,6 +263,7 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
     p.npw = npw;
     p.nchunks = (t->nnz + npw - 1) / npw;
     p.err = t->dev_err;
+    p.wait_tries = wait_tries();
     p.loss = -1;
     if (gcp) {
         if (kmode != M_SORTED || p.n_rb != 1)
@@ -346,3 +353,10 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
 }
 
 }  // namespace spt
+
+extern "C" spt_status spt_set_wait_tries(int64_t tries) {
+    if (tries < -1 || tries > (int64_t)UINT32_MAX)
+        return spt::fail(SPT_EINVAL, "spt_set_wait_tries: tries must be -1 (default) or in [0, 2^32 - 1]");
+    spt::g_wait_tries.store(tries < 0 ? SPT_WAIT_TRIES : (uint32_t)tries, std::memory_order_relaxed);
+    return SPT_OK;
+}

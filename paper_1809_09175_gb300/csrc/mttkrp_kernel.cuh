@@ -79,6 +79,8 @@ struct MttkrpParams {
     int npw;      // nonzeros per warp chunk = (32 >> log2L) * S, a multiple of 4
     int64_t nchunks;
     int *err;     // device status word
+    uint32_t wait_tries;  // try budget of a staging wait (the drain after a
+                          // timeout always uses the full SPT_WAIT_TRIES)
     // M_PRIVATE: the private output copy in shared memory
     int In;       // rows of the output (mode length)
     int pld;      // private row stride in accumulator elements, R rounded up to 4
@@ -729,7 +731,7 @@ __device__ __forceinline__ bool mttkrp_range(const MttkrpParams &p, uint64_t *ba
     for (int ch = ch_begin, kk = k0; ch < ch_end; ++ch, ++kk) {
         const int s = kk & 1;
         const uint32_t parity = (uint32_t)(kk >> 1) & 1u;
-        const bool ok = mbar_wait(&bars[s], parity);
+        const bool ok = mbar_wait(&bars[s], parity, p.wait_tries);
         if (!__all_sync(FULL, ok)) {
             // bounded-wait budget spent: report, let copies in flight land, leave
             if (lane == 0) atomicExch(p.err, SPT_DEV_TIMEOUT);
@@ -885,7 +887,7 @@ __device__ __forceinline__ void mttkrp_warp_range(const MttkrpParams &p, unsigne
     for (int ch = ch_begin; ch < ch_end; ++ch, ++k) {
         const int s = k & 1;
         const uint32_t parity = (uint32_t)(k >> 1) & 1u;
-        const bool ok = mbar_wait(&bars[s], parity);
+        const bool ok = mbar_wait(&bars[s], parity, p.wait_tries);
         if (!__all_sync(FULL, ok)) {
             // bounded-wait budget spent: report, let copies in flight land, leave
             if (lane == 0) atomicExch(p.err, SPT_DEV_TIMEOUT);

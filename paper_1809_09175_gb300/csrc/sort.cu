@@ -537,23 +537,16 @@ namespace {
 constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;  // 32 MiB per GPU
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[64] = {nullptr};
-
-// Device address of the scratch area on the current device.  The first call
-// on a device looks it up (with that device current); later calls reuse it.
+// Device address of the scratch area on the current device.  In host code
+// the array's name is only a host-side stand-in, so every call asks the
+// runtime for the address with the caller's device current (no allocation,
+// and never a stale address after a device reset re-creates the context).
+// The first lookup on a device also loads the library's device code there.
 spt_status noalloc_scratch(void **out) {
-    int dev = 0;
-    SPT_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(SPT_EUNSUPPORTED, "device index >= 64");
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
-        g_noalloc_ptr[dev] = p;
-    }
-    *out = g_noalloc_ptr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+    *out = p;
     return SPT_OK;
 }
 

@@ -39,6 +39,22 @@ def test_noalloc_permutation_matches_allocating_entry_point_twice():
         np.testing.assert_array_equal(perm.cpu().numpy(), _reference_perm(P, keys_np, dim))
 
 
+@pytest.mark.parametrize("n,dim", [(5000, 1), (70_001, 200), (1, 256), (300_000, 257), (123_457, 65_536)])
+def test_noalloc_one_and_two_pass_sorts_match(n, dim):
+    """Key ranges of one 8-bit digit (one pass, keys straight to perm), two
+    digits (two passes), and a single coordinate value (dim = 1)."""
+    import paper_1809_09175_gb300 as P
+    stream = torch.cuda.current_stream().cuda_stream
+    keys_np = np.random.default_rng(n + dim).integers(0, dim, n).astype(np.int32)
+    keys = torch.from_numpy(keys_np).cuda()
+    ref = _reference_perm(P, keys_np, dim)
+    for _ in range(2):  # the second call starts from the first call's scratch contents
+        perm = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        P.mode_permutation_noalloc(keys.data_ptr(), n, dim, perm.data_ptr(), stream)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(perm.cpu().numpy(), ref)
+
+
 def test_noalloc_rejects_sizes_beyond_the_scratch_area():
     import paper_1809_09175_gb300 as P
     keys = torch.zeros(8, dtype=torch.int32, device="cuda")
