@@ -66,6 +66,7 @@ spt_status free_tensor_buffers(spt_tensor t) {
     }
     dfree(t->coo_buf, st);
     dfree(t->dev_err, st);
+    dfree(t->hot_buf, st);
     cudaError_t e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? SPT_OK : cuda_fail(e, "tensor_destroy");
 }
@@ -162,6 +163,8 @@ spt_status tensor_create_coo(int order, const int64_t *dims, int64_t nnz,
         s = coalesce_tensor(t, st);
         if (s) { free_tensor_buffers(t); delete t; return s; }
     }
+    s = build_hot_rows(t, st);
+    if (s) { free_tensor_buffers(t); delete t; return s; }
     *out = t;
     return SPT_OK;
 }

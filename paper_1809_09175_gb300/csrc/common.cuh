@@ -22,6 +22,10 @@
 #define SPT_WAIT_TRIES (1u << 22)
 #define SPT_WAIT_HINT_NS 1000u
 
+// Hot rows kept per mode for the atomic scatter's shared-memory copy.
+#define SPT_HOT_MAX 256
+#define SPT_HOT_MIN_COUNT 1024
+
 struct ModeStats {
     bool valid = false;
     int64_t nonempty = 0;   // rows with at least one nonzero
@@ -55,6 +59,11 @@ struct spt_tensor_s {
     spt_dtype pref_fdt[SPT_MAX_ORDER] = {SPT_F32};
     spt_schedule pref[SPT_MAX_ORDER];
     int *dev_err = nullptr;  // device status word for kernels of this tensor
+    // per mode: the hottest rows (most nonzeros, at least SPT_HOT_MIN_COUNT,
+    // hottest first, ties in row order), up to SPT_HOT_MAX of them; the
+    // atomic scatter adds their row sums into shared memory (see mttkrp_kernel)
+    int32_t *hot_buf = nullptr;  // SPT_HOT_MAX entries per mode
+    int nhot[SPT_MAX_ORDER] = {0};
 };
 
 // ---- host error handling -------------------------------------------------

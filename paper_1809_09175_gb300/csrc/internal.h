@@ -16,6 +16,8 @@ spt_status radix_sort_pairs(const uint32_t *keys_in, const int32_t *vals_in, int
 spt_status coalesce_tensor(spt_tensor t, cudaStream_t st);
 spt_status build_perm_mode(spt_tensor t, int n, bool index_only, cudaStream_t st);
 spt_status compute_norm2(spt_tensor t, cudaStream_t st);
+// The hot-row list of every mode (t->hot_buf, t->nhot); synchronises `st`.
+spt_status build_hot_rows(spt_tensor t, cudaStream_t st);
 
 // Generalised CP arguments of a gradient launch (see gcp_gradient).
 struct GcpArgs {

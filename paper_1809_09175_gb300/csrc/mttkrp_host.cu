@@ -6,6 +6,12 @@
 #include "internal.h"
 #include "mttkrp_kernel.cuh"
 
+// Shared-memory bytes of the atomic scatter's per-CTA copy of the hot rows
+// (R = 16 fp32: 256 rows; R = 64: 64 rows).
+#ifndef SPT_HOT_SMEM
+#define SPT_HOT_SMEM (16 * 1024)
+#endif
+
 // 0: never take the clamped-gather kernels (build variant for comparisons)
 #ifndef SPT_CLAMP_GATHERS
 #define SPT_CLAMP_GATHERS 1
@@ -280,6 +286,21 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
     if (smem > 227 * 1024)
         return fail(SPT_EINVAL, "schedule: staging buffers exceed 227 KB of shared memory "
                                 "(lower warps_per_cta or nnz_per_group)");
+    if (kmode == M_ATOMIC && t->nhot[mode] > 0) {
+        // the mode's hottest rows go to a shared-memory copy per CTA: at most
+        // SPT_HOT_SMEM bytes of accumulators, and never past the 227 KB limit
+        const int pld = (rank + 3) & ~3;
+        int nhot = (int)std::min<int64_t>(t->nhot[mode], SPT_HOT_SMEM / ((int64_t)pld * ab));
+        auto log2T = [](int h) { return std::max(1, ilog2(2 * h)); };
+        while (nhot > 0 && smem + hot_smem_bytes(nhot, pld, ab, log2T(nhot)) > 227 * 1024) nhot >>= 1;
+        if (nhot > 0) {
+            p.hot_rows = t->hot_buf + (size_t)mode * SPT_HOT_MAX;
+            p.nhot = nhot;
+            p.hot_log2T = log2T(nhot);
+            p.pld = pld;
+            smem += hot_smem_bytes(nhot, pld, ab, p.hot_log2T);
+        }
+    }
     int K = 1;
     if (kmode == M_PRIVATE) {
         const int log2K = private_cluster_log2(t->dims[mode], rank, smem, ab);

@@ -20,7 +20,15 @@
 //      M_ATOMIC  storage order (coordinate arrays staged one by one); a
 //                group's running sum is added atomically (16-byte vector red)
 //                whenever its row changes (Fig. MTTKRP-B with merging of
-//                equal consecutive rows).
+//                equal consecutive rows).  The mode's hottest rows (a list
+//                made when the tensor is created) are the exception: their
+//                flushes are added into a per-CTA copy of those rows in
+//                shared memory (found through a small hash table), which the
+//                CTA adds to the output once at the end.  A row holding a
+//                large share of the nonzeros then takes one chain of adds per
+//                CTA instead of one serialised global chain as long as its
+//                nonzero count: faster, and without the rounding drift of
+//                millions of fp32 adds into one running value.
 //      M_SORTED  mode-n order from the mode-sorted copy, whose nonzeros are
 //                packed records {row, other coordinates, value} (one bulk copy
 //                and one vector shared load per nonzero);
@@ -81,9 +89,14 @@ struct MttkrpParams {
     int *err;     // device status word
     uint32_t wait_tries;  // try budget of a staging wait (the drain after a
                           // timeout always uses the full SPT_WAIT_TRIES)
+    // M_ATOMIC: the hot rows held in shared memory (nhot = 0: none)
+    const int32_t *hot_rows;  // nhot row ids, hottest first
+    int nhot;
+    int hot_log2T;            // hash table of 1 << hot_log2T slots (>= 2 nhot)
     // M_PRIVATE: the private output copy in shared memory
     int In;       // rows of the output (mode length)
-    int pld;      // private row stride in accumulator elements, R rounded up to 4
+    int pld;      // row stride of the shared-memory copy (private or hot rows) in
+                  // accumulator elements, R rounded up to 4
     int log2K;    // cluster size K = 1 << log2K CTAs share the rows
     int prows;    // private rows per CTA = ceil(In / K)
     // deterministic sums (sorted traversal with the run carry): the first and
@@ -148,6 +161,27 @@ __device__ __forceinline__ void chunk_bounds(const MttkrpParams &p, const int32_
     } else {
         b0 = b1 = -1;
     }
+}
+
+// Shared-memory layout of the atomic scatter's hot rows: nhot rows of pld
+// accumulators, then the hash table's keys (row ids, -1 = empty) and values
+// (slot of the row), 1 << hot_log2T of each.
+__host__ __device__ inline size_t hot_smem_bytes(int nhot, int pld, int ab, int log2T) {
+    return nhot > 0 ? (size_t)nhot * pld * ab + (size_t)2 * 4 * (1u << log2T) : 0;
+}
+
+// Slot of `row` among the hot rows, or -1 (linear probing; the table is at
+// most half full, so a miss stops at an empty slot within a few probes).
+__device__ __forceinline__ int hot_slot(const int *hkey, int log2T, int row) {
+    const unsigned mask = (1u << log2T) - 1u;
+    unsigned h = ((unsigned)row * 0x9E3779B1u) >> (32 - log2T);
+    for (unsigned q = 0; q <= mask; ++q) {
+        const int k = hkey[h];
+        if (k == row) return hkey[(1u << log2T) + h];
+        if (k < 0) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
 }
 
 // Compute one staged chunk of n nonzeros (n <= npw) for every rank block:
@@ -236,6 +270,19 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
                     }
                 }
                 return;
+            }
+            if (MODE == M_ATOMIC && priv) {  // a hot row: add into this CTA's shared copy
+                const int slot = hot_slot(reinterpret_cast<const int *>(priv + (int64_t)p.nhot * p.pld),
+                                          p.hot_log2T, row);
+                if (slot >= 0) {
+                    AT *hrow = priv + (int64_t)slot * p.pld;
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v)
+                            if (v < nv[c]) red_add_shared(smem_u32(hrow + col[c] + v), a[c][v] * lam[c][v]);
+                    return;
+                }
             }
             AT *dst = reinterpret_cast<AT *>(p.out) + (int64_t)row * p.old;
             if (DET && atomic && dslot >= 0) {  // deterministic: this warp's slot
@@ -963,9 +1010,53 @@ __device__ __forceinline__ void flush_private(const MttkrpParams &p, const AT *p
     }
 }
 
+// Atomic scatter with hot rows: zero this CTA's copy of the hot rows and
+// build the hash table, accumulate, then add the copy to the output (16-byte
+// vector atomics, all-zero quads skipped).  Every thread reaches both
+// barriers: warps without chunks (or whose wait ran out) skip to them.
+template <typename FT, int C, int D1>
+__device__ __forceinline__ void mttkrp_atomic_hot(const MttkrpParams &p, unsigned char *smem_raw) {
+    using AT = typename Elem<FT>::Acc;
+    const int wpc = blockDim.x >> 5;
+    AT *hot = reinterpret_cast<AT *>(smem_raw + warp_smem_bytes(wpc, C, 1 << p.log2L, (int)sizeof(AT),
+                                                                Staging<D1, M_ATOMIC>::WPE, p.npw));
+    int *hkey = reinterpret_cast<int *>(hot + (int64_t)p.nhot * p.pld);
+    const int T = 1 << p.hot_log2T;
+    for (int i = threadIdx.x; i < p.nhot * p.pld; i += blockDim.x) hot[i] = (AT)0;
+    for (int i = threadIdx.x; i < T; i += blockDim.x) hkey[i] = -1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < p.nhot; i += blockDim.x) {
+        const int row = __ldg(p.hot_rows + i);
+        unsigned h = ((unsigned)row * 0x9E3779B1u) >> (32 - p.hot_log2T);
+        for (int q = 0; q < T; ++q) {  // distinct rows: each claims the first free slot
+            if (atomicCAS(hkey + h, -1, row) == -1) {
+                hkey[T + h] = i;
+                break;
+            }
+            h = (h + 1) & (unsigned)(T - 1);
+        }
+    }
+    __syncthreads();
+    mttkrp_warp_range<FT, C, D1, M_ATOMIC>(p, smem_raw, hot);
+    __syncwarp();
+    __syncthreads();
+    const int q4 = p.pld >> 2;
+    for (int i = threadIdx.x; i < p.nhot * q4; i += blockDim.x) {
+        const int slot = i / q4, c4 = i - slot * q4;
+        const AT *src = hot + (int64_t)slot * p.pld + 4 * c4;
+        const AT v[4] = {src[0], src[1], src[2], src[3]};
+        if (v[0] != (AT)0 || v[1] != (AT)0 || v[2] != (AT)0 || v[3] != (AT)0)
+            red_add4(reinterpret_cast<AT *>(p.out) + (int64_t)__ldg(p.hot_rows + slot) * p.old + 4 * c4, v);
+    }
+}
+
 template <typename FT, int C, int D1, int MODE, bool CLAMP = false, bool DET = false>
 __global__ void __launch_bounds__(512, MinBlocks<FT, C>::value) mttkrp_kernel(const MttkrpParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (MODE == M_ATOMIC && p.nhot > 0) {
+        mttkrp_atomic_hot<FT, C, D1>(p, smem_raw);
+        return;
+    }
     if (MODE != M_PRIVATE) {
         mttkrp_warp_range<FT, C, D1, MODE, false, CLAMP, DET>(p, smem_raw, nullptr);
         return;

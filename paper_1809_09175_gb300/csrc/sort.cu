@@ -513,6 +513,88 @@ spt_status compute_norm2(spt_tensor t, cudaStream_t st) {
     return SPT_OK;
 }
 
+namespace {
+// flag[r] = 1 for rows with at least minc nonzeros
+__global__ void hot_flag_kernel(const int32_t *cnt, int64_t I, int32_t minc, int32_t *flag) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < I; r += (int64_t)gridDim.x * blockDim.x)
+        flag[r] = cnt[r] >= minc ? 1 : 0;
+}
+
+// candidates in row order: key = P - count (so an ascending sort puts the
+// hottest first), value = row
+__global__ void hot_compact_kernel(const int32_t *cnt, const int32_t *flag, const int32_t *pos, int64_t I,
+                                   uint32_t P, uint32_t *keys, int32_t *rows) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < I; r += (int64_t)gridDim.x * blockDim.x)
+        if (flag[r]) {
+            keys[pos[r]] = P - (uint32_t)cnt[r];
+            rows[pos[r]] = (int32_t)r;
+        }
+}
+}  // namespace
+
+// Per mode: count each row's nonzeros, keep the rows with at least
+// SPT_HOT_MIN_COUNT of them (in row order, by a flag scan), sort those by
+// count (stable, so ties stay in row order) and record the first SPT_HOT_MAX.
+spt_status build_hot_rows(spt_tensor t, cudaStream_t st) {
+    const int64_t P = t->nnz;
+    if (!t->hot_buf) {
+        spt_status s = dmalloc((void **)&t->hot_buf, sizeof(int32_t) * SPT_HOT_MAX * SPT_MAX_ORDER, st);
+        if (s) return s;
+    }
+    for (int n = 0; n < t->d; ++n) t->nhot[n] = 0;
+    if (P < SPT_HOT_MIN_COUNT) return SPT_OK;
+    for (int n = 0; n < t->d; ++n) {
+        const int64_t I = t->dims[n];
+        int32_t *cnt = nullptr, *flag = nullptr, *pos = nullptr, *total = nullptr, *rows = nullptr, *srows = nullptr;
+        uint32_t *keys = nullptr, *skeys = nullptr;
+        auto cleanup = [&]() {
+            dfree(cnt, st); dfree(flag, st); dfree(pos, st); dfree(total, st);
+            dfree(rows, st); dfree(srows, st); dfree(keys, st); dfree(skeys, st);
+        };
+        spt_status s = dmalloc((void **)&cnt, 4 * I, st);
+        if (!s) s = dmalloc((void **)&flag, 4 * I, st);
+        if (!s) s = dmalloc((void **)&pos, 4 * I, st);
+        if (!s) s = dmalloc((void **)&total, 4, st);
+        if (s) { cleanup(); return s; }
+        cudaError_t e = cudaMemsetAsync(cnt, 0, 4 * I, st);
+        if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "build_hot_rows memset"); }
+        slice_count_kernel<<<grid_for(P, 256), 256, 0, st>>>(t->idx[n], P, cnt);
+        hot_flag_kernel<<<grid_for(I, 256), 256, 0, st>>>(cnt, I, SPT_HOT_MIN_COUNT, flag);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "build_hot_rows kernels"); }
+        s = scan_exclusive(flag, pos, I, total, st);
+        int32_t nc = 0;
+        if (!s) {
+            e = cudaMemcpyAsync(&nc, total, 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) s = cuda_fail(e, "build_hot_rows count");
+        }
+        if (!s && nc > 0) {
+            s = dmalloc((void **)&keys, 4 * (size_t)nc, st);
+            if (!s) s = dmalloc((void **)&rows, 4 * (size_t)nc, st);
+            if (!s) s = dmalloc((void **)&skeys, 4 * (size_t)nc, st);
+            if (!s) s = dmalloc((void **)&srows, 4 * (size_t)nc, st);
+            if (!s) {
+                hot_compact_kernel<<<grid_for(I, 256), 256, 0, st>>>(cnt, flag, pos, I, (uint32_t)P, keys, rows);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) s = cuda_fail(e, "hot_compact_kernel");
+            }
+            if (!s) s = radix_sort_pairs(keys, rows, nc, bit_width_u32((uint64_t)P), skeys, srows, st);
+            const int k = std::min<int32_t>(nc, SPT_HOT_MAX);
+            if (!s) {
+                e = cudaMemcpyAsync(t->hot_buf + (size_t)n * SPT_HOT_MAX, srows, 4 * (size_t)k,
+                                    cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) s = cuda_fail(e, "build_hot_rows copy");
+            }
+            if (!s) t->nhot[n] = k;
+        }
+        cleanup();
+        if (s) return s;
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? SPT_OK : cuda_fail(e, "build_hot_rows");
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free mode permutation.
 //

@@ -313,3 +313,34 @@ def test_fp64_outside_mttkrp_is_unsupported():
         T.cp_als_step(facs, 8, lam, None, ws)
     assert ei.value.status == P.SPT_EUNSUPPORTED
     T.close()
+
+
+def _hot_row_tensor(dims, nnz, hot, seed):
+    """Uniform coordinates, except that `hot` nonzeros at random storage
+    positions share mode-0 row 7 (a row far hotter than any real-world slice
+    of this size: every atomic flush of it lands on one output row)."""
+    rng = np.random.default_rng(seed)
+    idx = np.stack([rng.integers(0, I, nnz) for I in dims]).astype(np.int32)
+    idx[0, rng.choice(nnz, hot, replace=False)] = 7
+    return idx, rng.uniform(0.0, 1.0, nnz).astype(np.float32)
+
+
+@pytest.mark.parametrize("scatter", SCATTERS)
+@pytest.mark.parametrize("dist,R", [("normal", 16), ("uniform", 32)])
+def test_row_with_two_million_nonzeros(scatter, dist, R):
+    """One row holds 2.2e6 of 3e6 nonzeros in random storage order: every
+    scatter (the atomic one adds such a row through its shared-memory copy
+    of the hot rows) must stay within the fp32 gate on every mode."""
+    P = _lib()
+    dims = (5000, 3000, 2000)
+    idx, vals = _hot_row_tensor(dims, 3_000_000, 2_200_000, 31)
+    facs = synth.factor_matrices(dims, R, 31, dist)
+    outs = _run(P, idx, vals, dims, facs, "f32", R, scatter)
+    for n in range(3):
+        if outs[n] is None:
+            continue
+        ref = _oracle(idx, vals, dims, facs, "f32", R, n)
+        err = rel_fro(outs[n][:, :R], ref)
+        assert err <= TOL["f32"], (n, err)
+        if n == 0:  # the hot row by itself
+            assert rel_fro(outs[n][7, :R], ref[7]) <= TOL["f32"], n
