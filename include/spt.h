@@ -151,6 +151,17 @@ spt_status tensor_check(spt_tensor t, void *stream);
  * radix sort borrows 16P bytes of temporary device memory. */
 spt_status build_mode_permutation(spt_tensor t, int mode, int flags, void *stream);
 
+/* A new tensor holding the nonzeros at positions [begin, end) of the mode-n
+ * permutation of t (perm_n order: increasing mode-n coordinate), with t's
+ * dims: the piece of t one process or GPU owns when the nonzeros are split
+ * into contiguous ranges of perm_n (the multi-GPU distribution Sec. 8 names
+ * as future work).  The shard is coalesced if t is (a subset of distinct
+ * coordinates), with its own ||X||^2.  Needs build_mode_permutation(mode)
+ * (SPT_ESTATE otherwise); SPT_EINVAL unless 0 <= begin <= end <= nnz.
+ * Synchronises `stream`.  Free with tensor_destroy. */
+spt_status tensor_create_shard(spt_tensor t, int mode, int64_t begin, int64_t end, void *stream,
+                               spt_tensor *out);
+
 /* Copy perm_n (P int32) to a caller device buffer. SPT_ESTATE if not built. */
 spt_status tensor_get_permutation(spt_tensor t, int mode, int32_t *perm, void *stream);
 
@@ -458,6 +469,51 @@ spt_status cp_als_workspace_size(spt_tensor t, int rank, int ld, size_t *bytes);
 spt_status cp_als_step(spt_tensor t, void *const *factors, spt_dtype fdt, int rank, int ld,
                        double *lambda, double *fit_out, void *workspace, size_t workspace_bytes,
                        void *stream);
+
+/* The steps of one CP-ALS mode update (Sec. 3 ALS; cp_als_step runs the same
+ * kernels), one call each, for a caller that splits the nonzeros -- and so
+ * the rows of V -- across processes or GPUs and exchanges the partial sums
+ * itself (the multi-GPU distribution Sec. 8 names as future work): per mode
+ * n, V = the mode-n MTTKRP of its nonzeros (mttkrp) summed over the pieces,
+ * then cp_als_hinv, cp_als_apply on its rows of V, a sum of colsq over the
+ * pieces, cp_als_normalize, cp_als_gram on its rows of the new factor, a sum
+ * of the Grams over the pieces, and the factor rows gathered back; after
+ * the last mode, cp_als_fit.  Stream-ordered, no synchronisation.
+ *
+ * cp_als_hinv: H = elementwise product over m != mode of the R x R FP64
+ *   Grams G (device, order * R * R doubles, G_m at G + m R R); Cholesky
+ *   H = L L^T in FP64 with one retry at a ridge of 1e-12 trace(H)/R; hinv
+ *   (device, R * R float32) = H^-1.  If H is not positive definite after the
+ *   ridge, *status (device int) is set to 2 and hinv to the identity. */
+spt_status cp_als_hinv(const double *G, int order, int mode, int rank, float *hinv, int *status, void *stream);
+
+/* cp_als_apply: A32 = V hinv for `rows` rows of V (device, rows x ld float32,
+ *   columns >= rank zero) into A32 (device, rows x ld float32, columns >=
+ *   rank not written), and colsq[j] += sum over the rows of A32(:, j)^2
+ *   (device, rank doubles; the caller zeroes it).  FP32 FMAs, FP64 sums. */
+spt_status cp_als_apply(const float *V, int64_t rows, int ld, int rank, const float *hinv, float *A32,
+                        double *colsq, void *stream);
+
+/* cp_als_normalize: lambda_j = sqrt(colsq_j) (device, rank doubles, the
+ *   sums over ALL rows), A = A32 / lambda in the factor type fdt (device,
+ *   rows x ld, padding columns zero, 16-bit types rounded to nearest even; a
+ *   zero column is kept).  With V and inner (both device, or both NULL):
+ *   inner += sum V(k, j) lambda_j A(k, j) over these rows (the <X, M> term of
+ *   the fit from the last mode's V; the caller zeroes it). */
+spt_status cp_als_normalize(const float *A32, const float *V, int64_t rows, int ld, int rank, const double *colsq,
+                            void *A, spt_dtype fdt, double *lambda, double *inner, void *stream);
+
+/* cp_als_gram: G += A^T A over `rows` rows of A (device, rows x ld of fdt),
+ *   G device R x R FP64 (FP32 partial sums over at most 256 rows, added in
+ *   FP64; the caller zeroes G). */
+spt_status cp_als_gram(const void *A, int64_t rows, int ld, int rank, spt_dtype fdt, double *G, void *stream);
+
+/* cp_als_fit: fit = 1 - sqrt(max(0, xnorm2 + ||M||^2 - 2 inner)) / sqrt(xnorm2)
+ *   with ||M||^2 = lambda^T (*_m G_m) lambda (G: order Grams as for
+ *   cp_als_hinv); *inner (device double, the summed <X, M>) is read and then
+ *   set to 0; *fit is a device double. */
+spt_status cp_als_fit(const double *G, int order, int rank, const double *lambda, double *inner, double xnorm2,
+                      double *fit, void *stream);
 
 /* Device status word of the last cp_als_step on this workspace (synchronises
  * `stream`): SPT_OK or SPT_ESINGULAR. */

@@ -10,5 +10,6 @@ in ``libspt.so`` (hand-written CUDA for sm_103a behind the C ABI of
 from . import binding  # noqa: F401  (fails loudly if libspt.so is missing)
 from .binding import *  # noqa: F401,F403
 from .tensor import SparseTensor, factor_ld  # noqa: F401
+from . import shard  # noqa: F401  (nonzero-sharded CP-ALS over a process group)
 
-__all__ = ["binding", "SparseTensor", "factor_ld"] + list(binding.EXPORTED)
+__all__ = ["binding", "shard", "SparseTensor", "factor_ld"] + list(binding.EXPORTED)

@@ -157,6 +157,12 @@ _try_sig("mttkrp_batch_info", _vp, _i64p, _i64p, C.POINTER(C.c_int))
 _try_sig("mttkrp_batch_check", _vp, _vp)
 _try_sig("mttkrp_batch_destroy", _vp)
 _try_sig("spt_set_wait_tries", C.c_int64)
+_try_sig("tensor_create_shard", _vp, C.c_int, C.c_int64, C.c_int64, _vp, C.POINTER(_vp))
+_try_sig("cp_als_hinv", _vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp)
+_try_sig("cp_als_apply", _vp, C.c_int64, C.c_int, C.c_int, _vp, _vp, _vp, _vp)
+_try_sig("cp_als_normalize", _vp, _vp, C.c_int64, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp, _vp, _vp)
+_try_sig("cp_als_gram", _vp, C.c_int64, C.c_int, C.c_int, C.c_int, _vp, _vp)
+_try_sig("cp_als_fit", _vp, C.c_int, C.c_int, _vp, _vp, C.c_double, _vp, _vp)
 SPT_NOALLOC_MAX_NNZ = 1835008
 
 
@@ -313,6 +319,37 @@ def cp_als_step(t: int, factor_ptrs: Sequence[int], fdt, rank: int, ld: int, lam
 
 def cp_als_status(workspace_ptr: int, stream: int = 0):
     _chk(_L.cp_als_status(workspace_ptr, stream or None))
+
+
+def tensor_create_shard(t: int, mode: int, begin: int, end: int, stream: int = 0) -> int:
+    """Handle of a new tensor holding perm_n positions [begin, end) of t."""
+    out = _vp()
+    _chk(_L.tensor_create_shard(t, mode, int(begin), int(end), stream or None, C.byref(out)))
+    return out.value
+
+
+def cp_als_hinv(G_ptr: int, order: int, mode: int, rank: int, hinv_ptr: int, status_ptr: int, stream: int = 0):
+    _chk(_L.cp_als_hinv(G_ptr, order, mode, rank, hinv_ptr, status_ptr, stream or None))
+
+
+def cp_als_apply(V_ptr: int, rows: int, ld: int, rank: int, hinv_ptr: int, A32_ptr: int, colsq_ptr: int,
+                 stream: int = 0):
+    _chk(_L.cp_als_apply(V_ptr or None, int(rows), ld, rank, hinv_ptr, A32_ptr or None, colsq_ptr, stream or None))
+
+
+def cp_als_normalize(A32_ptr: int, V_ptr: Optional[int], rows: int, ld: int, rank: int, colsq_ptr: int, A_ptr: int,
+                     fdt, lambda_ptr: int, inner_ptr: Optional[int], stream: int = 0):
+    _chk(_L.cp_als_normalize(A32_ptr or None, V_ptr or None, int(rows), ld, rank, colsq_ptr, A_ptr or None,
+                             _dt(fdt), lambda_ptr, inner_ptr or None, stream or None))
+
+
+def cp_als_gram(A_ptr: int, rows: int, ld: int, rank: int, fdt, G_ptr: int, stream: int = 0):
+    _chk(_L.cp_als_gram(A_ptr or None, int(rows), ld, rank, _dt(fdt), G_ptr, stream or None))
+
+
+def cp_als_fit(G_ptr: int, order: int, rank: int, lambda_ptr: int, inner_ptr: int, xnorm2: float, fit_ptr: int,
+               stream: int = 0):
+    _chk(_L.cp_als_fit(G_ptr, order, rank, lambda_ptr, inner_ptr, float(xnorm2), fit_ptr, stream or None))
 
 
 def spt_set_wait_tries(tries: int):

@@ -58,6 +58,16 @@ __global__ void range_check_kernel(IdxSet s, int d, int64_t n, unsigned long lon
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(bad, c);
 }
 
+// Shard of a tensor: nonzero i of the shard is nonzero perm[begin + i] of t.
+__global__ void shard_gather_kernel(IdxSet src, const float *vals, const int32_t *perm, int64_t begin, int64_t n,
+                                    int d, IdxSet dst_idx, float *dst_vals) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = perm[begin + i];
+        for (int m = 0; m < d; ++m) const_cast<int32_t *>(dst_idx.p[m])[i] = src.p[m][q];
+        dst_vals[i] = vals[q];
+    }
+}
+
 spt_status free_tensor_buffers(spt_tensor t) {
     cudaStream_t st = 0;
     for (int n = 0; n < SPT_MAX_ORDER; ++n) {
@@ -166,6 +176,53 @@ spt_status tensor_create_coo(int order, const int64_t *dims, int64_t nnz,
     s = build_hot_rows(t, st);
     if (s) { free_tensor_buffers(t); delete t; return s; }
     *out = t;
+    return SPT_OK;
+}
+
+spt_status tensor_create_shard(spt_tensor t, int mode, int64_t begin, int64_t end, void *stream, spt_tensor *out) {
+    if (!t || !out) return fail(SPT_EINVAL, "tensor_create_shard: NULL argument");
+    *out = nullptr;
+    if (mode < 0 || mode >= t->d) return fail(SPT_EINVAL, "tensor_create_shard: mode out of range");
+    if (begin < 0 || end < begin || end > t->nnz)
+        return fail(SPT_EINVAL, "tensor_create_shard: need 0 <= begin <= end <= nnz");
+    if (!t->perm[mode]) return fail(SPT_ESTATE, "tensor_create_shard: needs build_mode_permutation(mode)");
+    cudaStream_t st = (cudaStream_t)stream;
+    spt_tensor s = new (std::nothrow) spt_tensor_s();
+    if (!s) return fail(SPT_ENOMEM, "tensor_create_shard: host allocation failed");
+    cudaGetDevice(&s->device);
+    s->d = t->d;
+    for (int m = 0; m < t->d; ++m) s->dims[m] = t->dims[m];
+    const int64_t n = end - begin;
+    s->nnz = n;
+    const size_t seg = seg_bytes(n, 4);
+    spt_status c = dmalloc(&s->coo_buf, seg * (t->d + 1), st);
+    if (!c) c = dmalloc((void **)&s->dev_err, sizeof(int), st);
+    if (c) { free_tensor_buffers(s); delete s; return c; }
+    IdxSet src, dst;
+    for (int m = 0; m < t->d; ++m) {
+        s->idx[m] = reinterpret_cast<int32_t *>((char *)s->coo_buf + seg * m);
+        src.p[m] = t->idx[m];
+        dst.p[m] = s->idx[m];
+    }
+    s->vals = reinterpret_cast<float *>((char *)s->coo_buf + seg * t->d);
+    cudaError_t e = cudaMemsetAsync(s->dev_err, 0, sizeof(int), st);
+    if (e == cudaSuccess && n > 0) {
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, sm_count() * 8));
+        shard_gather_kernel<<<grid, 256, 0, st>>>(src, t->vals, t->perm[mode], begin, n, t->d, dst, s->vals);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        c = cuda_fail(e, "tensor_create_shard");
+        free_tensor_buffers(s);
+        delete s;
+        return c;
+    }
+    // a subset of distinct coordinates is coalesced too; its ||X||^2 is its own
+    s->coalesced = t->coalesced;
+    c = s->coalesced ? compute_norm2(s, st) : SPT_OK;
+    if (!c) c = build_hot_rows(s, st);
+    if (c) { free_tensor_buffers(s); delete s; return c; }
+    *out = s;
     return SPT_OK;
 }
 

@@ -185,12 +185,13 @@ __global__ void __launch_bounds__(1024) gram_kernel(const FT *A, int64_t I, int 
     }
 }
 
-// H = *_{m != n} G_m; zero G_n and the column sums for this mode's update;
-// Cholesky (one retry with ridge 1e-12 trace/R); Hinv = L^-T L^-1 -> float.
+// H = *_{m != n} G_m; Cholesky (one retry with ridge 1e-12 trace/R);
+// Hinv = L^-T L^-1 -> float.  zero_gram / zero_colsq (nullable): R*R and R
+// doubles cleared afterwards for this mode's update (G_n and the column sums).
 // Shared memory: R*R doubles (L in the lower triangle, W = L^-1 strictly
 // below the diagonal stored transposed in the upper triangle) + R doubles.
-__global__ void __launch_bounds__(512) chol_inv_kernel(double *G, int d, int n, int R, float *Hinv,
-                                                       double *colsq, int *status) {
+__global__ void __launch_bounds__(512) chol_inv_kernel(const double *G, int d, int n, int R, float *Hinv,
+                                                       double *zero_gram, double *zero_colsq, int *status) {
     extern __shared__ double sh[];
     double *Hs = sh;            // R x R
     double *Wd = sh + R * R;    // R: diagonal of W
@@ -268,8 +269,11 @@ __global__ void __launch_bounds__(512) chol_inv_kernel(double *G, int d, int n, 
             Hinv[e] = (float)sacc;
         }
     }
-    for (int e = threadIdx.x; e < RR; e += blockDim.x) G[(int64_t)n * RR + e] = 0.0;
-    for (int r = threadIdx.x; r < R; r += blockDim.x) colsq[r] = 0.0;
+    __syncthreads();  // every thread has read G before G_n is cleared
+    if (zero_gram)
+        for (int e = threadIdx.x; e < RR; e += blockDim.x) zero_gram[e] = 0.0;
+    if (zero_colsq)
+        for (int r = threadIdx.x; r < R; r += blockDim.x) zero_colsq[r] = 0.0;
 }
 
 // A32 = V Hinv, column sums of squares.  Thread (rq, cq) computes the 4 x 4
@@ -570,7 +574,8 @@ spt_status enqueue_step(spt_tensor t, void *const *factors, spt_dtype fdt, int R
         spt_schedule sc = default_schedule(t, n, fdt, R);
         spt_status s = launch_mttkrp(t, n, factors, fdt, R, ld, nullptr, w.V, sc, st);
         if (s) return s;
-        chol_inv_kernel<<<1, 512, chol_smem, st>>>(w.G, d, n, R, w.Hinv, w.colsq, w.status);
+        chol_inv_kernel<<<1, 512, chol_smem, st>>>(w.G, d, n, R, w.Hinv, w.G + (size_t)n * R * R, w.colsq,
+                                                   w.status);
         SPT_LAUNCH_CHECK("chol_inv_kernel");
         const int CT = (R + 3) / 4;
         const int trows = 4 * (256 / CT);
@@ -685,6 +690,90 @@ spt_status cp_als_step(spt_tensor t, void *const *factors, spt_dtype fdt, int ra
         return SPT_OK;
     }
     return enqueue_step(t, factors, fdt, rank, ld, lambda, fit_out, w, st);
+}
+
+// ---- the steps of a CP-ALS mode update, one call each, for callers that
+// split the rows of V (and the nonzeros) across processes or GPUs -----------
+
+spt_status cp_als_hinv(const double *G, int order, int mode, int rank, float *hinv, int *status, void *stream) {
+    if (!G || !hinv || !status) return fail(SPT_EINVAL, "cp_als_hinv: NULL argument");
+    if (order < 1 || order > SPT_MAX_KERNEL_ORDER || mode < 0 || mode >= order)
+        return fail(SPT_EINVAL, "cp_als_hinv: order in [1, 5] and mode in [0, order)");
+    if (rank < 1 || rank > MAXR) return fail(SPT_EUNSUPPORTED, "cp_als_hinv: rank must be in [1, 128]");
+    spt_status a = ensure_cpals_attrs();
+    if (a) return a;
+    cudaStream_t st = (cudaStream_t)stream;
+    chol_inv_kernel<<<1, 512, sizeof(double) * (rank * rank + rank), st>>>(G, order, mode, rank, hinv, nullptr,
+                                                                             nullptr, status);
+    SPT_LAUNCH_CHECK("chol_inv_kernel");
+    return SPT_OK;
+}
+
+spt_status cp_als_apply(const float *V, int64_t rows, int ld, int rank, const float *hinv, float *A32,
+                        double *colsq, void *stream) {
+    if (rows < 0 || (rows > 0 && (!V || !A32)) || !hinv || !colsq) return fail(SPT_EINVAL, "cp_als_apply: NULL argument");
+    if (rank < 1 || rank > MAXR) return fail(SPT_EUNSUPPORTED, "cp_als_apply: rank must be in [1, 128]");
+    if (ld < rank || ld % 8) return fail(SPT_EINVAL, "cp_als_apply: ld must be >= rank and a multiple of 8");
+    if (((uintptr_t)V | (uintptr_t)A32) & 15) return fail(SPT_EINVAL, "cp_als_apply: V and A32 must be 16-byte aligned");
+    spt_status a = ensure_cpals_attrs();
+    if (a) return a;
+    if (rows == 0) return SPT_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int CT = (rank + 3) / 4;
+    const int trows = 4 * (256 / CT);
+    const size_t smem = sizeof(float) * ((size_t)rank * CT * 4 + (size_t)2 * trows * (CT * 4 + 4));
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + trows - 1) / trows, sm_count() * 2));
+    solve_kernel<<<blocks, 256, smem, st>>>(V, rows, ld, rank, hinv, A32, colsq);
+    SPT_LAUNCH_CHECK("solve_kernel");
+    return SPT_OK;
+}
+
+spt_status cp_als_normalize(const float *A32, const float *V, int64_t rows, int ld, int rank, const double *colsq,
+                            void *A, spt_dtype fdt, double *lambda, double *inner, void *stream) {
+    if (rows < 0 || (rows > 0 && (!A32 || !A)) || !colsq || !lambda)
+        return fail(SPT_EINVAL, "cp_als_normalize: NULL argument");
+    if ((V == nullptr) != (inner == nullptr)) return fail(SPT_EINVAL, "cp_als_normalize: V and inner go together");
+    if (rank < 1 || rank > MAXR) return fail(SPT_EUNSUPPORTED, "cp_als_normalize: rank must be in [1, 128]");
+    if (ld < rank || ld % 8) return fail(SPT_EINVAL, "cp_als_normalize: ld must be >= rank and a multiple of 8");
+    if (fdt != SPT_F32 && fdt != SPT_BF16 && fdt != SPT_F16) return fail(SPT_EINVAL, "cp_als_normalize: bad dtype");
+    if (((uintptr_t)A32 | (uintptr_t)V | (uintptr_t)A) & 15)
+        return fail(SPT_EINVAL, "cp_als_normalize: A32, V and A must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int rpp = std::max(1, 256 / (ld / 4));
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + rpp - 1) / rpp, sm_count() * 8));
+    const int last = inner ? 1 : 0;
+    if (fdt == SPT_F32)
+        normalize_kernel<float><<<blocks, 256, 0, st>>>(A32, V, rows, ld, rank, colsq, (float *)A, lambda, last, inner);
+    else if (fdt == SPT_BF16)
+        normalize_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(A32, V, rows, ld, rank, colsq, (__nv_bfloat16 *)A,
+                                                                lambda, last, inner);
+    else
+        normalize_kernel<__half><<<blocks, 256, 0, st>>>(A32, V, rows, ld, rank, colsq, (__half *)A, lambda, last,
+                                                         inner);
+    SPT_LAUNCH_CHECK("normalize_kernel");
+    return SPT_OK;
+}
+
+spt_status cp_als_gram(const void *A, int64_t rows, int ld, int rank, spt_dtype fdt, double *G, void *stream) {
+    if (rows < 0 || (rows > 0 && !A) || !G) return fail(SPT_EINVAL, "cp_als_gram: NULL argument");
+    if (rank < 1 || rank > MAXR) return fail(SPT_EUNSUPPORTED, "cp_als_gram: rank must be in [1, 128]");
+    if (ld < rank || ld % 8) return fail(SPT_EINVAL, "cp_als_gram: ld must be >= rank and a multiple of 8");
+    if (fdt != SPT_F32 && fdt != SPT_BF16 && fdt != SPT_F16) return fail(SPT_EINVAL, "cp_als_gram: bad dtype");
+    if ((uintptr_t)A & 15) return fail(SPT_EINVAL, "cp_als_gram: A must be 16-byte aligned");
+    spt_status a = ensure_cpals_attrs();
+    if (a) return a;
+    if (rows == 0) return SPT_OK;
+    return gram_any(fdt, A, rows, ld, rank, G, (cudaStream_t)stream);
+}
+
+spt_status cp_als_fit(const double *G, int order, int rank, const double *lambda, double *inner, double xnorm2,
+                      double *fit, void *stream) {
+    if (!G || !lambda || !inner || !fit) return fail(SPT_EINVAL, "cp_als_fit: NULL argument");
+    if (order < 1 || order > SPT_MAX_KERNEL_ORDER) return fail(SPT_EINVAL, "cp_als_fit: order in [1, 5]");
+    if (rank < 1 || rank > MAXR) return fail(SPT_EUNSUPPORTED, "cp_als_fit: rank must be in [1, 128]");
+    fit_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(G, order, rank, lambda, inner, xnorm2, fit);
+    SPT_LAUNCH_CHECK("fit_kernel");
+    return SPT_OK;
 }
 
 spt_status cp_als_status(void *workspace, void *stream) {

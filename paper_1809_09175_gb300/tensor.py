@@ -56,6 +56,17 @@ class SparseTensor:
         self.coalesced = bool(fl & B.SPT_COALESCE)
         self.order = d
 
+    @classmethod
+    def from_handle(cls, handle: int, dims: Sequence[int]) -> "SparseTensor":
+        """Wrap a library tensor handle (e.g. from tensor_create_shard); the
+        wrapper owns it and destroys it on close()."""
+        self = cls.__new__(cls)
+        self.handle = handle
+        self.dims = [int(x) for x in dims]
+        self.order, _, self.nnz, fl = B.tensor_info(handle)
+        self.coalesced = bool(fl & B.SPT_COALESCE)
+        return self
+
     def close(self):
         if getattr(self, "handle", None):
             B.tensor_destroy(self.handle)
