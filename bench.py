@@ -64,6 +64,8 @@ def parse():
                     help="instead: the paper's 30K x 40K x 50K / 1e7-nonzero tensor, MTTKRP for R = 8..256 "
                          "step 8 with fp64, fp32 and bf16 factors, and 10 CP-ALS iterations at R = 128")
     ap.add_argument("--sweep-ranks", default="8:257:8", help="start:stop:step of the rank sweep")
+    ap.add_argument("--gather-probe", type=float, default=0,
+                    help="time factor-row gathers for this many nonzeros (loads vs TMA) and exit")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1809_09175_gb300",
                                                        "selector_weights.npz"))
     return ap.parse_args()
@@ -750,13 +752,17 @@ def run_cpals(args):
         chosen = [net.choose(T, n, R, fdt) for n in range(d)]
         t_select = time.perf_counter() - t0
         scheds["selector"] = [c[0] for c in chosen]
-        ranks, sel_mode_ms = [], []
+        ranks, sel_mode_ms, kept = [], [], []
         for n in range(d):
             cands, valid = P.mttkrp_candidates(T.handle, n, R)
             order = [q for q in np.argsort(chosen[n][1]) if valid[q]]
             tt = np.array(auto_times[n])
             ranks.append(order.index(int(np.argmin(np.where(tt > 0, tt, np.inf)))))
-            sel_mode_ms.append(float(tt[order[0]]))
+            out = torch.empty((w.dims[n], ld), device="cuda")
+            sel_mode_ms.append(P.mttkrp_time_schedule(T.handle, n, ptrs, fdt, R, ld, out.data_ptr(),
+                                                      chosen[n][0], 3, st))
+            kept.append(chosen[n][0].as_dict() == scheds["default"][n].as_dict())
+            del out
         t0 = time.perf_counter()
         ver = []
         for n in range(d):
@@ -767,6 +773,8 @@ def run_cpals(args):
         scheds["selector_verified"] = [v[0] for v in ver]
         sel_info = {"rank_of_exhaustive_best_in_network_order": ranks,
                     "selector_mttkrp_ms_per_mode": sel_mode_ms,
+                    "selector_kept_default_per_mode": kept, "anchor_margin": net.anchor_margin,
+                    "exhaustive_mttkrp_ms_per_mode": auto_ms,
                     "verified_mttkrp_ms_per_mode": [v[1] for v in ver],
                     "verify_s": t_verify}
     res = {}
@@ -891,12 +899,39 @@ def run_batched(args):
     e1.record()
     torch.cuda.synchronize()
     single_ms = e0.elapsed_time(e1) / args.steps
+    # each task's kernel alone (fastest of 3 launches, output zeroing included)
+    task_ms = 0.0
+    for T, facs, outs, sc, w in zip(Ts, facs_all, outs_all, tuned, specs):
+        for n in range(len(w.dims)):
+            task_ms += P.mttkrp_time_schedule(T.handle, n, [f.data_ptr() for f in facs], fdt, w.R,
+                                              facs[0].shape[1], outs[n].data_ptr(), sc[n], 3)
+    # bytes: the survey's algorithmic figure (sorted traversal, cache hits not
+    # deducted) and a compulsory one: every output written once, every record
+    # read once, and each factor's distinct touched rows (at most min(I_m, P))
+    # read once
+    s_f = 4 if fdt == "f32" else 2
+    alg = comp = 0
+    for w in specs:
+        d_ = len(w.dims)
+        ld_ = P.factor_ld(w.R)
+        for n in range(d_):
+            alg += algorithmic_bytes("sorted", w.nnz, d_, w.R, s_f, w.dims[n], w.dims[n])
+            comp += (w.dims[n] * ld_ * 4 + w.nnz * 4 * {2: 4, 3: 4, 4: 6, 5: 6}[d_]
+                     + sum(min(w.dims[m], w.nnz) * ld_ * s_f for m in range(d_) if m != n))
+    peak, peak_kind = measured_peaks()
     line = {"metric": METRIC, "workload": f"batched{len(specs)}", "tensors": len(specs),
             "total_nnz": int(sum(w.nnz for w in specs)), "tasks": ntask, "work_items": nitem,
             "persistent_ctas": blocks, "factors": fdt, "setup_s": setup_s,
             "batched_ms": batch_ms, "batched_nnzR_per_s": units / (batch_ms / 1e3),
             "per_task_launches_ms": single_ms, "per_task_nnzR_per_s": units / (single_ms / 1e3),
-            "speedup": single_ms / batch_ms, "launches_per_run": 2, "graph": True}
+            "sum_of_task_kernel_ms": task_ms,
+            "speedup": single_ms / batch_ms, "launches_per_run": 1 + len({(s_.chunks, len(w.dims) == 5) for w, sc in zip(specs, tuned) for s_ in sc}),
+            "graph": True,
+            "bytes": {"algorithmic": alg, "compulsory": comp,
+                      "algorithmic_GBps": alg / (batch_ms / 1e3) / 1e9,
+                      "compulsory_GBps": comp / (batch_ms / 1e3) / 1e9,
+                      "compulsory_frac": comp / (batch_ms / 1e3) / 1e9 / peak, "peak": peak,
+                      "peak_kind": peak_kind}}
     print(json.dumps(line), flush=True)
     P.mttkrp_batch_destroy(b)
     for T in Ts:
@@ -1024,10 +1059,52 @@ def run_paper_sweep(args):
     T.close()
 
 
+def run_gather_probe(args):
+    """The ceiling of the MTTKRP's gather step: 64-byte factor rows (fp32,
+    R = 16) of the 3-way 1e8 workload's mode-1 and mode-2 factors (5e5 and
+    2e5 rows, Zipf s = 1.2 row streams) brought to the SMs by 16-byte loads
+    (the kernel's way), by TMA tile::gather4 and by 1-D bulk copies, each
+    into a product, without the nonzero records or the scatter."""
+    import torch
+    import paper_1809_09175_gb300 as P
+    import synth
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n = int(args.gather_probe) // 64 * 64
+    dims = (500_000, 200_000)
+    idx, _ = synth.coo_zipf_device(dims, n, 1.2, 5)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    F = [torch.rand((I, 16), generator=g, device="cuda") for I in dims]
+    sink = torch.zeros(1, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream()
+    out = {"metric": "factor-row gather rate (64-byte rows, two per nonzero)", "nonzeros": n,
+           "rows": list(dims), "zipf_s": 1.2, "unit": "rows/s", "methods": {}}
+    for m, name in ((0, "ld.global 16 B per lane"), (1, "TMA tile::gather4"), (2, "1-D cp.async.bulk per row")):
+        def launch():
+            P.spt_row_gather_probe(m, F[0].data_ptr(), dims[0], F[1].data_ptr(), dims[1], idx[0].data_ptr(),
+                                   idx[1].data_ptr(), n, sink.data_ptr(), status.data_ptr(), st.cuda_stream)
+        launch()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(5):
+            launch()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        out["methods"][name] = {"ms": ms, "rows_per_s": 2 * n / (ms / 1e3), "ms_per_1e8_nonzeros": ms * 1e8 / n}
+    out["status"] = int(status.item())
+    print(json.dumps(out), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.gather_probe:
+        run_gather_probe(a)
     elif a.paper_sweep:
         run_paper_sweep(a)
     elif a.cpals:

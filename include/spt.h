@@ -309,9 +309,11 @@ spt_status mttkrp_time_schedule(spt_tensor t, int mode, const void *const *facto
                                 float *ms, void *stream);
 
 /* Exhaustive autotuner: time every valid candidate (mttkrp_time_schedule)
- * and return the fastest in *best (and its time in *best_ms).  times
- * (nullable, SPT_NUM_CANDIDATES floats, host) receives every candidate's
- * time, -1 for invalid ones: the training data of the learned selector.
+ * and the library's own rule (mttkrp_default_schedule without a recorded
+ * preference), and return the fastest in *best (and its time in *best_ms).
+ * times (nullable, SPT_NUM_CANDIDATES floats, host) receives every
+ * candidate's time, -1 for invalid ones: the training data of the learned
+ * selector.
  * `out` is scratch output (I_mode x ld float32).  Synchronises `stream`. */
 spt_status mttkrp_autotune(spt_tensor t, int mode, const void *const *factors, spt_dtype fdt, int rank,
                            int ld, void *out, int reps, spt_schedule *best, float *best_ms,
@@ -358,12 +360,18 @@ typedef struct {
     const float *params;
     const float *mean;
     const float *std;
+    float anchor_margin; /* >= 0: the outputs are log(candidate time / time of the
+                          * schedule mttkrp() runs for sched == NULL), and that
+                          * schedule is kept unless the best valid prediction is
+                          * below -anchor_margin; < 0: the outputs are relative
+                          * log times and the smallest always wins */
 } spt_selector;
 
 /* Choose a schedule with a trained selector: features -> network (own
- * inference kernel) -> the valid candidate with the smallest predicted time.
- * pred (nullable, host, SPT_NUM_CANDIDATES) receives the predictions.
- * Synchronises `stream`. */
+ * inference kernel) -> the valid candidate with the smallest predicted time,
+ * or (anchor_margin >= 0) mttkrp_default_schedule's choice when no candidate
+ * is predicted to beat it by more than the margin.  pred (nullable, host,
+ * SPT_NUM_CANDIDATES) receives the predictions.  Synchronises `stream`. */
 spt_status mttkrp_select(spt_tensor t, int mode, spt_dtype fdt, int rank, const spt_selector *sel,
                          spt_schedule *out, float *pred, void *stream);
 
@@ -393,15 +401,18 @@ typedef struct {
 } spt_batch_item;
 
 /* Build a batch: one task per (tensor, mode); tasks are grouped by kernel
- * class (chunks per lane, order), and each class's task chunks, cut into
- * blocks of 8, form its work list.  Copies the task tables to the device
+ * class (chunks per lane, and order 5 apart from orders 2..4: one class for
+ * tensors of order up to 4 and ranks up to 128 with the library's
+ * schedules), and each class's task chunks, cut into blocks of 8, form its
+ * work list.  Copies the task tables to the device
  * (synchronous); the pointers are captured, so the tensors, factors and
  * outputs must outlive the batch and keep their addresses. */
 spt_status mttkrp_batch_create(int count, const spt_batch_item *items, spt_dtype fdt, spt_batch *out);
 
 /* Run every task: one zero-fill kernel for the outputs and counters, then
  * one persistent kernel per class whose warps claim blocks of chunks from
- * the class's device counter.  On a non-default stream the launches are
+ * the class's device counter and run each with the routine of its task's
+ * order.  On a non-default stream the launches are
  * captured in a CUDA graph at the first call and replayed afterwards; on the
  * legacy default stream they are launched directly. */
 spt_status mttkrp_batch_run(spt_batch b, void *stream);
@@ -534,6 +545,21 @@ spt_status spt_stream_copy(const void *src, void *dst, size_t bytes, void *strea
  * launch with events on `stream` to get the device's FMA throughput.  sink is
  * a device double that the kernel never writes in practice. */
 spt_status spt_fma_probe(spt_dtype dt, int64_t iters, double *sink, double *flops, void *stream);
+
+/* Factor-row gather probe (no counterpart in the paper; the ceiling of the
+ * MTTKRP's gather step): for i < n, bring row r1[i] of F1 and row r2[i] of
+ * F2 (row-major, 16 float32 columns = 64 bytes per row, I1 and I2 rows) to
+ * the SMs and multiply them, by
+ *   method 0: 16-byte global loads, 4 lanes per row (the MTTKRP kernel's way);
+ *   method 1: TMA tile::gather4 into shared memory (four rows per instruction);
+ *   method 2: one 1-D bulk copy per row into shared memory.
+ * Enqueues one launch on `stream`; time it with events.  n a multiple of 64;
+ * every pointer device, 16-byte aligned; sink a device float the kernel
+ * never writes in practice; status a device int set to 1 if a bounded wait
+ * of methods 1 and 2 ran out. */
+spt_status spt_row_gather_probe(int method, const float *F1, int64_t I1, const float *F2, int64_t I2,
+                                const int32_t *r1, const int32_t *r2, int64_t n, float *sink, int *status,
+                                void *stream);
 
 /* Convert n float32 values to fdt storage (round to nearest even). */
 spt_status spt_convert_f32(const float *src, void *dst, spt_dtype fdt, int64_t n, void *stream);

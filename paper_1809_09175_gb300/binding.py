@@ -54,7 +54,7 @@ class spt_schedule(C.Structure):
 class spt_selector(C.Structure):
     _fields_ = [("F", C.c_int), ("H1", C.c_int), ("H2", C.c_int), ("K", C.c_int),
                 ("params", C.c_void_p), ("mean", C.POINTER(C.c_float)),
-                ("std", C.POINTER(C.c_float))]
+                ("std", C.POINTER(C.c_float)), ("anchor_margin", C.c_float)]
 
 
 class spt_batch_item(C.Structure):
@@ -157,6 +157,7 @@ _try_sig("mttkrp_batch_info", _vp, _i64p, _i64p, C.POINTER(C.c_int))
 _try_sig("mttkrp_batch_check", _vp, _vp)
 _try_sig("mttkrp_batch_destroy", _vp)
 _try_sig("spt_set_wait_tries", C.c_int64)
+_try_sig("spt_row_gather_probe", C.c_int, _vp, C.c_int64, _vp, C.c_int64, _vp, _vp, C.c_int64, _vp, _vp, _vp)
 _try_sig("tensor_create_shard", _vp, C.c_int, C.c_int64, C.c_int64, _vp, C.POINTER(_vp))
 _try_sig("cp_als_hinv", _vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp)
 _try_sig("cp_als_apply", _vp, C.c_int64, C.c_int, C.c_int, _vp, _vp, _vp, _vp)
@@ -350,6 +351,13 @@ def cp_als_gram(A_ptr: int, rows: int, ld: int, rank: int, fdt, G_ptr: int, stre
 def cp_als_fit(G_ptr: int, order: int, rank: int, lambda_ptr: int, inner_ptr: int, xnorm2: float, fit_ptr: int,
                stream: int = 0):
     _chk(_L.cp_als_fit(G_ptr, order, rank, lambda_ptr, inner_ptr, float(xnorm2), fit_ptr, stream or None))
+
+
+def spt_row_gather_probe(method: int, F1_ptr: int, I1: int, F2_ptr: int, I2: int, r1_ptr: int, r2_ptr: int,
+                         n: int, sink_ptr: int, status_ptr: int, stream: int = 0):
+    """Enqueue the factor-row gather probe (method 0 loads, 1 TMA gather4, 2 bulk copies)."""
+    _chk(_L.spt_row_gather_probe(method, F1_ptr, I1, F2_ptr, I2, r1_ptr, r2_ptr, n, sink_ptr, status_ptr,
+                                 stream or None))
 
 
 def spt_set_wait_tries(tries: int):

@@ -3,14 +3,15 @@
 // Every (tensor, mode) pair is a task; a task's nonzeros (its mode-sorted
 // packed records) are cut into chunks of its schedule's npw nonzeros, and a
 // task's chunks into blocks of BATCH_BLOCK_CHUNKS.  Tasks are grouped by
-// kernel class (chunks per lane C, order - 1): every class runs one
-// persistent kernel specialised for it, whose warps claim blocks with an
-// atomic counter (uneven tensors balance themselves) and walk each block as
-// a contiguous range with the single-tensor kernel's range routine: staged
-// bulk copies, the segmented combine and the run carried across the block's
-// chunks (Sec. 6 permuted traversal over sorted nonzeros, Fig. MTTKRP-C).
-// One zero-fill kernel clears every output and the counters first; the
-// launches are captured once in a CUDA graph and replayed.
+// kernel class, the chunks per lane C (1 for every rank up to 128 with the
+// library's schedules): every class runs one persistent kernel whose warps
+// claim blocks with an atomic counter (uneven tensors balance themselves),
+// switch on the task's order, and walk each block as a contiguous range with
+// the single-tensor kernel's range routine: staged bulk copies, the segmented
+// combine and the run carried across the block's chunks (Sec. 6 permuted
+// traversal over sorted nonzeros, Fig. MTTKRP-C).  One zero-fill kernel
+// clears every output and the counters first; the launches are captured
+// once in a CUDA graph and replayed.
 #include <vector>
 
 #include "internal.h"
@@ -24,6 +25,7 @@ constexpr int BATCH_BLOCK_CHUNKS = 8;  // chunks a warp claims at a time
 struct BatchTask {
     MttkrpParams p;       // M_SORTED parameters of this (tensor, mode)
     int64_t first_block;  // first block of this task in its class's block space
+    int d1;               // order - 1 of the tensor
 };
 
 struct ZeroSeg {
@@ -52,10 +54,13 @@ __device__ __forceinline__ int find_task(const BatchTask *tasks, int ntasks, int
     return lo;
 }
 
-// Persistent kernel of one class (FT, C, D1).  Shared memory per warp: two
-// barriers (first 16 * wpc bytes), a carry slot of cb bytes, two staging
-// buffers of stage_words words each (the largest task of the class).
-template <typename FT, int C, int D1>
+// Persistent kernel of one class (FT, C, orders up to 4 or order 5); each
+// block runs the range routine of its task's order (order 5 has a kernel of
+// its own: its extra gathers would make the others spill).  Shared memory
+// per warp: two barriers (first 16 * wpc bytes), a carry slot of cb bytes,
+// two staging buffers of stage_words words each (the largest task of the
+// class).
+template <typename FT, int C, bool ORDER5>
 __global__ void __launch_bounds__(256, C == 1 ? 3 : 2)
     mttkrp_batch_kernel(const BatchTask *__restrict__ tasks, int ntasks, int64_t total_blocks,
                         unsigned long long *counter, int stage_words, int cb) {
@@ -79,13 +84,24 @@ __global__ void __launch_bounds__(256, C == 1 ? 3 : 2)
         const MttkrpParams &p = tasks[t].p;  // read through the cache, not copied to registers
         const int64_t c0 = (blk - tasks[t].first_block) * BATCH_BLOCK_CHUNKS;
         const int64_t c1 = c0 + BATCH_BLOCK_CHUNKS < p.nchunks ? c0 + BATCH_BLOCK_CHUNKS : p.nchunks;
-        if (!mttkrp_range<FT, C, D1, M_SORTED>(p, bars, carry, wbuf, nullptr, (int)c0, (int)c1, k)) return;
+        bool ok;
+        if (ORDER5) {
+            ok = mttkrp_range<FT, C, 4, M_SORTED>(p, bars, carry, wbuf, nullptr, (int)c0, (int)c1, k);
+        } else {
+            switch (tasks[t].d1) {  // warp-uniform
+                case 1: ok = mttkrp_range<FT, C, 1, M_SORTED>(p, bars, carry, wbuf, nullptr, (int)c0, (int)c1, k); break;
+                case 2: ok = mttkrp_range<FT, C, 2, M_SORTED>(p, bars, carry, wbuf, nullptr, (int)c0, (int)c1, k); break;
+                default: ok = mttkrp_range<FT, C, 3, M_SORTED>(p, bars, carry, wbuf, nullptr, (int)c0, (int)c1, k); break;
+            }
+        }
+        if (!ok) return;
     }
 }
 
-// One class of tasks: kernel (C, D1), its task table and launch shape.
+// One class of tasks: kernel (C, order 5 or not), its task table and launch shape.
 struct BatchClass {
-    int C = 1, D1 = 2;
+    int C = 1;
+    bool order5 = false;
     std::vector<BatchTask> htasks;
     BatchTask *dtasks = nullptr;
     int64_t total_blocks = 0;
@@ -95,19 +111,17 @@ struct BatchClass {
     int blocks = 0;
 };
 
-template <typename FT> const void *class_fn(int C, int D1) {
-    static const void *tab[2][4] = {
-        {(const void *)mttkrp_batch_kernel<FT, 1, 1>, (const void *)mttkrp_batch_kernel<FT, 1, 2>,
-         (const void *)mttkrp_batch_kernel<FT, 1, 3>, (const void *)mttkrp_batch_kernel<FT, 1, 4>},
-        {(const void *)mttkrp_batch_kernel<FT, 2, 1>, (const void *)mttkrp_batch_kernel<FT, 2, 2>,
-         (const void *)mttkrp_batch_kernel<FT, 2, 3>, (const void *)mttkrp_batch_kernel<FT, 2, 4>}};
-    return (C >= 1 && C <= 2 && D1 >= 1 && D1 <= 4) ? tab[C - 1][D1 - 1] : nullptr;
+template <typename FT> const void *class_fn(int C, bool order5) {
+    static const void *tab[2][2] = {
+        {(const void *)mttkrp_batch_kernel<FT, 1, false>, (const void *)mttkrp_batch_kernel<FT, 1, true>},
+        {(const void *)mttkrp_batch_kernel<FT, 2, false>, (const void *)mttkrp_batch_kernel<FT, 2, true>}};
+    return (C >= 1 && C <= 2) ? tab[C - 1][order5 ? 1 : 0] : nullptr;
 }
 
-const void *batch_fn(spt_dtype fdt, int C, int D1) {
-    return fdt == SPT_F32    ? class_fn<float>(C, D1)
-           : fdt == SPT_BF16 ? class_fn<__nv_bfloat16>(C, D1)
-                             : class_fn<__half>(C, D1);
+const void *batch_fn(spt_dtype fdt, int C, bool order5) {
+    return fdt == SPT_F32    ? class_fn<float>(C, order5)
+           : fdt == SPT_BF16 ? class_fn<__nv_bfloat16>(C, order5)
+                             : class_fn<__half>(C, order5);
 }
 
 int ilog2i(int x) {
@@ -148,7 +162,7 @@ spt_status enqueue_batch(spt_batch b, cudaStream_t st) {
         unsigned long long *cnt = b->counters + c;
         int sw = k.stage_words, cb = k.cb;
         void *args[] = {(void *)&dt, (void *)&nt, (void *)&tb, (void *)&cnt, (void *)&sw, (void *)&cb};
-        SPT_CUDA(cudaLaunchKernel(batch_fn(b->fdt, k.C, k.D1), dim3(k.blocks), dim3(b->wpc * 32), args, k.smem, st));
+        SPT_CUDA(cudaLaunchKernel(batch_fn(b->fdt, k.C, k.order5), dim3(k.blocks), dim3(b->wpc * 32), args, k.smem, st));
     }
     return SPT_OK;
 }
@@ -199,7 +213,12 @@ spt_status mttkrp_batch_create(int count, const spt_batch_item *items, spt_dtype
             BatchTask tk{};
             MttkrpParams &p = tk.p;
             const int L = sc.lanes_per_nnz, C = sc.chunks, G = 32 / L;
-            int S = std::max(1, sc.nnz_per_group);  // same bank rule as the single kernel
+            // one class kernel serves every task, and its staging is sized for
+            // the largest chunk: cap each task's chunk at the default rule's
+            // 6 KB of shared memory per warp, so one task with long chunks
+            // does not cut the occupancy of the whole batch
+            const int npw_cap = std::max(G, (6144 - 16 - carry_bytes(C, L, 4)) / (8 * record_words(t->d)));
+            int S = std::max(1, std::min(sc.nnz_per_group, std::max(1, npw_cap / G)));  // same bank rule as the single kernel
             if (G >= 4) S = (S & 1) ? S : S - 1;
             else if (G == 2) S = std::max(2, (S & ~3) | 2);
             else S = std::max(4, (S + 3) & ~3);
@@ -234,14 +253,16 @@ spt_status mttkrp_batch_create(int count, const spt_batch_item *items, spt_dtype
             b->hsegs.push_back(ZeroSeg{o, t->dims[n] * (int64_t)it.ld});
             ++b->ntasks;
             if (t->nnz == 0) continue;  // zero-filled, nothing to add
+            tk.d1 = t->d - 1;
+            const bool o5 = t->d == 5;
             BatchClass *cls = nullptr;
             for (auto &k : b->classes)
-                if (k.C == C && k.D1 == t->d - 1) cls = &k;
+                if (k.C == C && k.order5 == o5) cls = &k;
             if (!cls) {
                 b->classes.emplace_back();
                 cls = &b->classes.back();
                 cls->C = C;
-                cls->D1 = t->d - 1;
+                cls->order5 = o5;
             }
             tk.first_block = cls->total_blocks;
             cls->total_blocks += (p.nchunks + BATCH_BLOCK_CHUNKS - 1) / BATCH_BLOCK_CHUNKS;
@@ -262,7 +283,7 @@ spt_status mttkrp_batch_create(int count, const spt_batch_item *items, spt_dtype
         k.stage_words = (k.stage_words + 3) & ~3;  // 16-byte aligned staging buffers
         k.smem = 16 * (size_t)b->wpc + (size_t)b->wpc * k.cb + (size_t)b->wpc * 2 * k.stage_words * 4;
         if (k.smem > 227 * 1024) { free_batch(b); return fail(SPT_EINVAL, "mttkrp_batch_create: staging exceeds shared memory"); }
-        const void *fn = batch_fn(fdt, k.C, k.D1);
+        const void *fn = batch_fn(fdt, k.C, k.order5);
         if (!fn) { free_batch(b); return fail(SPT_EUNSUPPORTED, "mttkrp_batch_create: no kernel for this class"); }
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
         int bps = 0;

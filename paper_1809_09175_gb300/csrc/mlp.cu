@@ -265,6 +265,12 @@ spt_status mttkrp_select(spt_tensor t, int mode, spt_dtype fdt, int rank, const 
         if (valid[q] && (bq < 0 || y[q] < y[bq])) bq = q;
     if (pred)
         for (int q = 0; q < SPT_NUM_CANDIDATES; ++q) pred[q] = y[q];
+    if (sel->anchor_margin >= 0.f && (bq < 0 || y[bq] >= -sel->anchor_margin)) {
+        // outputs are relative to the library's own choice: keep it unless a
+        // candidate is predicted to beat it by more than the margin
+        *out = default_schedule(t, mode, fdt, rank);
+        return SPT_OK;
+    }
     if (bq < 0) return fail(SPT_EUNSUPPORTED, "mttkrp_select: no valid candidate");
     *out = cand[bq];
     return SPT_OK;

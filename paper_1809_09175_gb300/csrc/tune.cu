@@ -114,8 +114,26 @@ spt_status mttkrp_autotune(spt_tensor t, int mode, const void *const *factors, s
         }
         if (times) times[q] = ms;
     }
+    // the library's own rule is timed too, so the tuner never returns a
+    // schedule slower than running without it (the rule's chunk sizes lie
+    // between the candidates' and often win on large tensors)
+    spt_schedule pick = bq >= 0 ? candidate(bq, rank) : spt_schedule{};
+    const bool had_pref = t->pref_set[mode];
+    t->pref_set[mode] = false;  // the rule itself, not a recorded choice
+    const spt_schedule rule = default_schedule(t, mode, fdt, rank);
+    t->pref_set[mode] = had_pref;
+    if (check_schedule(t, mode, fdt, rank, rule) == SPT_OK) {
+        float ms = -1.f;
+        spt_status s = mttkrp_time_schedule(t, mode, factors, fdt, rank, ld, out, &rule, reps, &ms, stream);
+        if (s) return s;
+        if (ms < bms) {
+            bms = ms;
+            pick = rule;
+            bq = SPT_NUM_CANDIDATES;
+        }
+    }
     if (bq < 0) return fail(SPT_EUNSUPPORTED, "mttkrp_autotune: no valid candidate");
-    *best = candidate(bq, rank);
+    *best = pick;
     if (best_ms) *best_ms = bms;
     return SPT_OK;
 }

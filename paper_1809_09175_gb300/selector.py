@@ -5,9 +5,11 @@ Sec. 5).  Here the exhaustive autotuner (``mttkrp_autotune``) times every
 candidate schedule of a (tensor, mode, rank, dtype); those timings train a
 small network (``mlp_*`` kernels: forward, back-propagation, Adam, all in
 ``libspt.so``) that maps the mode's features (``tensor_mode_features``) to
-the predicted log time of each candidate, and ``mttkrp_select`` picks the
-candidate with the smallest prediction using the network's fused inference
-kernel.  This module only marshals data between those entry points.
+the predicted log time of each candidate relative to the library's own
+choice (``mttkrp_default_schedule``), and ``mttkrp_select`` picks the
+candidate with the smallest prediction -- keeping the library's choice unless
+a candidate is predicted to beat it by more than ``ANCHOR_MARGIN`` -- using
+the network's fused inference kernel.  This module only marshals data between those entry points.
 """
 from __future__ import annotations
 
@@ -44,13 +46,21 @@ def collect(T, factors: List[torch.Tensor], rank: int, fdt: str, reps: int = 1):
     return rows
 
 
-def targets(times: np.ndarray, weighting: str = "sqrt"):
-    """Regression targets: log(time / best time) of each valid candidate;
-    mask 0 where a candidate could not run.  With weighting "sqrt" a sample's
-    mask is sqrt(its best time / the mean best time), so the fit favours the
-    tensors that dominate total run time over launch-overhead noise of tiny
-    ones; "none" weighs every sample alike."""
+# The network's outputs are log(candidate time / time of the library's own
+# choice, mttkrp_default_schedule), so a negative output is a predicted gain
+# over running without the selector; mttkrp_select keeps the library's
+# choice unless some candidate is predicted to beat it by more than this.
+ANCHOR_MARGIN = 0.02
+
+
+def targets(times: np.ndarray, t_default: np.ndarray, weighting: str = "sqrt"):
+    """Regression targets: log(time / default-rule time) of each valid
+    candidate; mask 0 where a candidate could not run.  With weighting
+    "sqrt" a sample's mask is sqrt(its best time / the mean best time), so
+    the fit favours the tensors that dominate total run time over
+    launch-overhead noise of tiny ones; "none" weighs every sample alike."""
     times = np.asarray(times, np.float64)
+    t_default = np.asarray(t_default, np.float64)
     valid = times > 0
     T = np.zeros(times.shape, np.float32)
     M = valid.astype(np.float32)
@@ -59,21 +69,34 @@ def targets(times: np.ndarray, weighting: str = "sqrt"):
         v = valid[b]
         if v.any():
             best[b] = times[b, v].min()
-            T[b, v] = np.log(times[b, v] / best[b])
+            T[b, v] = np.log(times[b, v] / t_default[b])
     if weighting == "sqrt":
         M *= np.sqrt(best / best.mean()).astype(np.float32)[:, None]
     return T, M
+
+
+def pick(pred: np.ndarray, times: np.ndarray, t_default: float, margin: float) -> float:
+    """Time of the schedule the anchored rule selects for one sample: the
+    best-predicted valid candidate if it is predicted to beat the default by
+    more than `margin`, else the default."""
+    v = times > 0
+    if not v.any():
+        return float(t_default)
+    y = np.where(v, pred, np.inf)
+    q = int(np.argmin(y))
+    return float(times[q]) if (margin < 0 or y[q] < -margin) else float(t_default)
 
 
 class Net:
     """Parameters (device, packed as the kernels expect) and feature scaling."""
 
     def __init__(self, params: torch.Tensor, mean: np.ndarray, std: np.ndarray,
-                 h1: int = H1, h2: int = H2):
+                 h1: int = H1, h2: int = H2, anchor_margin: float = ANCHOR_MARGIN):
         self.params = params
         self.mean = np.ascontiguousarray(mean, np.float32)
         self.std = np.ascontiguousarray(std, np.float32)
         self.h1, self.h2 = h1, h2
+        self.anchor_margin = float(anchor_margin)
 
     @staticmethod
     def init(seed: int = 0, h1: int = H1, h2: int = H2, mean=None, std=None):
@@ -140,7 +163,8 @@ class Net:
                       np.ascontiguousarray(self.std, np.float32))
         fp = B.C.POINTER(B.C.c_float)
         return B.spt_selector(F, self.h1, self.h2, K, self.params.data_ptr(),
-                              self._keep[0].ctypes.data_as(fp), self._keep[1].ctypes.data_as(fp))
+                              self._keep[0].ctypes.data_as(fp), self._keep[1].ctypes.data_as(fp),
+                              self.anchor_margin)
 
     def choose(self, T, mode: int, rank: int, fdt: str):
         """The selector's schedule for (tensor, mode, rank, dtype)."""
@@ -170,7 +194,7 @@ class Net:
 
     def save(self, path: str):
         np.savez(path, params=self.params.cpu().numpy(), mean=self.mean, std=self.std,
-                 h1=self.h1, h2=self.h2)
+                 h1=self.h1, h2=self.h2, anchor_margin=self.anchor_margin)
 
     @staticmethod
     def load(path: str) -> "Net":
@@ -180,7 +204,9 @@ class Net:
         if z["params"].size != want or z["mean"].size != F or z["std"].size != F:
             raise ValueError(f"{path}: a network for {z['params'].size} parameters, this library's "
                              f"candidate list needs {want} ({K} outputs); retrain it")
-        return Net(torch.from_numpy(z["params"]).cuda(), z["mean"], z["std"], h1, h2)
+        # weights saved without a margin predict log(time / best time): no anchor
+        margin = float(z["anchor_margin"]) if "anchor_margin" in z else -1.0
+        return Net(torch.from_numpy(z["params"]).cuda(), z["mean"], z["std"], h1, h2, margin)
 
 
 def fit_scaling(X: np.ndarray):
