@@ -51,6 +51,8 @@ def parse():
                     help="nonzeros of the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the variants / CP-ALS extras")
+    ap.add_argument("--slice-order", type=int, default=1,
+                    help="1: build the mode-sorted copies with each slice ordered by the next modes")
     ap.add_argument("--full-parity-s", type=float, default=120.0,
                     help="whole-output parity against the all-core oracle when its estimated time "
                          "is within this many seconds (0: off)")
@@ -64,6 +66,8 @@ def parse():
                     help="instead: the paper's 30K x 40K x 50K / 1e7-nonzero tensor, MTTKRP for R = 8..256 "
                          "step 8 with fp64, fp32 and bf16 factors, and 10 CP-ALS iterations at R = 128")
     ap.add_argument("--sweep-ranks", default="8:257:8", help="start:stop:step of the rank sweep")
+    ap.add_argument("--shard-cpals", type=int, default=0,
+                    help="time this many CP-ALS iterations with the nonzeros split across the ranks (NCCL)")
     ap.add_argument("--gather-probe", type=float, default=0,
                     help="time factor-row gathers for this many nonzeros (loads vs TMA) and exit")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1809_09175_gb300",
@@ -295,7 +299,7 @@ def run_ours(args):
     T = P.SparseTensor(idx, vals, w.dims)
     torch.cuda.synchronize()
     t_perm = time.perf_counter()
-    T.build_permutation(-1, index_only=(args.scatter == "perm"))
+    T.build_permutation(-1, index_only=(args.scatter == "perm"), slice_order=bool(args.slice_order))
     torch.cuda.synchronize()
     t_done = time.perf_counter()
     ingest_s, perm_s = t_perm - t_ing, t_done - t_perm
@@ -483,6 +487,7 @@ def run_ours(args):
                    "schedule": args.sched if args.sched == "default" else
                    "exhaustive autotune per mode (untimed set-up, %.1f s)" % tune_s,
                    "step": "MTTKRP of every mode (one launch per mode)",
+                   "slice_order": bool(args.slice_order),
                    "l2": "inputs larger than L2 (COO stream "
                    f"{w.nnz * 4 * (d + 1) / 1e9:.1f} GB per mode pass)"},
         "per_mode_ms": mode_ms,
@@ -663,7 +668,7 @@ def measure_extras(args, P, torch, w, T, idx, vals, facs_np, dtype, R, d, ld, ou
     # ---- CP-ALS iterations on the coalesced tensor (duplicates summed)
     Tc = P.SparseTensor(idx, vals, w.dims, coalesce=True)
     t0 = time.perf_counter()
-    Tc.build_permutation()
+    Tc.build_permutation()  # plain copies: over a few iterations the slice order's longer build does not pay
     torch.cuda.synchronize()
     sort_s = time.perf_counter() - t0
     fc = [_dev_factor(torch, f, dtype) for f in facs_np]
@@ -1059,6 +1064,92 @@ def run_paper_sweep(args):
     T.close()
 
 
+def run_shard_cpals(args):
+    """CP-ALS with the nonzeros split across the ranks (one per GPU, NCCL):
+    every rank holds a contiguous range of each mode's permutation, V is
+    reduce-scattered by row blocks, the Grams and column norms all-reduced,
+    the factor rows all-gathered (paper Sec. 8 future work).  The workload's
+    tensor is coalesced; `--shard-cpals K` timed iterations after --warmup,
+    the slowest rank's time.  With one rank, cp_als_step on the same GPU is
+    timed beside it (the cost of the split and of the collectives' calls)."""
+    import socket
+    import torch
+    import torch.distributed as dist
+    import paper_1809_09175_gb300 as P
+    from paper_1809_09175_gb300 import shard as S
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if "MASTER_ADDR" not in os.environ:  # one rank started without torchrun
+        os.environ["MASTER_ADDR"] = "127.0.0.1"
+        so = socket.socket()
+        so.bind(("127.0.0.1", 0))
+        os.environ["MASTER_PORT"] = str(so.getsockname()[1])
+        so.close()
+    dist.init_process_group("nccl", rank=rank, world_size=world, device_id=torch.device("cuda", local))
+    w = synth.workload(args.workload, args.scale)
+    fdt = args.dtype or w.factor_dtype
+    R, d = w.R, len(w.dims)
+    ld = P.factor_ld(R)
+    idx, vals = synth.coo_zipf_device(w.dims, w.nnz, w.s, w.seed)
+    T = P.SparseTensor(idx, vals, w.dims, coalesce=True)
+    del idx, vals
+    T.build_permutation()
+    shards = S.make_shards(T, world, rank)
+    facs_np = w.factors(R, fdt)
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[fdt]
+    facs = [torch.from_numpy(f.view(np.int16) if fdt != "f32" else f).cuda().view(tdt) for f in facs_np]
+    drv = S.ShardedCPALS(S.DeviceOps(T, shards, R, fdt, ld), w.dims, R, ld)
+    F = drv.padded_factors(facs)
+    lam = torch.zeros(R, dtype=torch.float64, device="cuda")
+    fit = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        drv.step(F, lam, fit)
+    torch.cuda.synchronize()
+    dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.shard_cpals):
+        drv.step(F, lam, fit)
+    e1.record()
+    torch.cuda.synchronize()
+    dist.barrier()
+    t = torch.tensor([e0.elapsed_time(e1) / args.shard_cpals], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    s_f = 4 if fdt == "f32" else 2
+    comm = sum(S.row_block(I, world) * world * ld * (4 + s_f) for I in w.dims) + (2 * d + 1) * R * R * 8
+    line = {"metric": "sharded CP-ALS iter/s", "workload": w.name, "n_gpus": world, "nnz_coalesced": T.nnz,
+            "R": R, "factors": fdt, "iterations": args.shard_cpals, "warmup": args.warmup,
+            "ms_per_iter": ms, "iter_per_s": 1e3 / ms, "fit": float(fit.item()),
+            "collective_bytes_per_rank_per_iter": comm,
+            "collectives": "per mode: reduce-scatter of V (fp32), all-reduce of the column norms and of "
+                           "the R x R FP64 Gram, all-gather of the factor rows"}
+    if world == 1:  # the unsplit iteration on the same GPU
+        g = [torch.from_numpy(f.view(np.int16) if fdt != "f32" else f).cuda().view(tdt) for f in facs_np]
+        ws = T.cp_als_workspace(R, ld)
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            for _ in range(args.warmup):
+                T.cp_als_step(g, R, lam, fit, ws)
+            e0.record(side)
+            for _ in range(args.shard_cpals):
+                T.cp_als_step(g, R, lam, fit, ws)
+            e1.record(side)
+        torch.cuda.synchronize()
+        line["cp_als_step_ms_per_iter"] = e0.elapsed_time(e1) / args.shard_cpals
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for s_ in shards:
+        s_.close()
+    T.close()
+    dist.destroy_process_group()
+
+
 def run_gather_probe(args):
     """The ceiling of the MTTKRP's gather step: 64-byte factor rows (fp32,
     R = 16) of the 3-way 1e8 workload's mode-1 and mode-2 factors (5e5 and
@@ -1081,10 +1172,31 @@ def run_gather_probe(args):
     st = torch.cuda.current_stream()
     out = {"metric": "factor-row gather rate (64-byte rows, two per nonzero)", "nonzeros": n,
            "rows": list(dims), "zipf_s": 1.2, "unit": "rows/s", "methods": {}}
-    for m, name in ((0, "ld.global 16 B per lane"), (1, "TMA tile::gather4"), (2, "1-D cp.async.bulk per row")):
+    # the same rows, ordered by (row of F1, row of F2) within segments of
+    # `seg` nonzeros, as a slice's nonzeros would be if the mode-sorted copy
+    # ordered each slice by the other modes
+    def sorted_within(seg):
+        key = idx[0].long() * dims[1] + idx[1].long()
+        if seg >= n:
+            order = torch.argsort(key, stable=True)
+        else:
+            base = (torch.arange(n, device="cuda") // seg) * (dims[0] * dims[1])
+            order = torch.argsort(base + key, stable=True)
+        return idx[0][order].contiguous(), idx[1][order].contiguous()
+    streams = {"random order": (idx[0], idx[1])}
+    for seg in (184, 4096, n):
+        streams[f"sorted within {seg}"] = sorted_within(seg)
+    runs = [(0, "ld.global 16 B per lane", "random order"), (1, "TMA tile::gather4", "random order"),
+            (2, "1-D cp.async.bulk per row", "random order")]
+    for sname in list(streams)[1:]:
+        runs += [(0, "ld.global 16 B per lane", sname), (3, "ld.global, groups on consecutive nonzeros", sname)]
+    for m, mname, sname in runs:
+        name = f"{mname} / {sname}"
+        r1, r2 = streams[sname]
+
         def launch():
-            P.spt_row_gather_probe(m, F[0].data_ptr(), dims[0], F[1].data_ptr(), dims[1], idx[0].data_ptr(),
-                                   idx[1].data_ptr(), n, sink.data_ptr(), status.data_ptr(), st.cuda_stream)
+            P.spt_row_gather_probe(m, F[0].data_ptr(), dims[0], F[1].data_ptr(), dims[1], r1.data_ptr(),
+                                   r2.data_ptr(), n, sink.data_ptr(), status.data_ptr(), st.cuda_stream)
         launch()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -1105,6 +1217,8 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.gather_probe:
         run_gather_probe(a)
+    elif a.shard_cpals:
+        run_shard_cpals(a)
     elif a.paper_sweep:
         run_paper_sweep(a)
     elif a.cpals:

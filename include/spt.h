@@ -56,7 +56,8 @@ typedef enum { SPT_F32 = 0, SPT_BF16 = 1, SPT_F16 = 2, SPT_F64 = 3 } spt_dtype;
 #define SPT_COALESCE 2    /* sum duplicate coordinates; output in lexicographic order */
 
 /* build_mode_permutation flags */
-#define SPT_PERM_INDEX_ONLY 1 /* keep only the permutation, not the mode-sorted copy */
+#define SPT_PERM_INDEX_ONLY 1  /* keep only the permutation, not the mode-sorted copy */
+#define SPT_PERM_SLICE_ORDER 2 /* order each slice of the mode-sorted copy by the next modes */
 
 /* Scatter strategies of the MTTKRP (Sec. 4-6). */
 typedef enum {
@@ -145,7 +146,11 @@ spt_status tensor_check(spt_tensor t, void *stream);
  * increasing mode-n coordinate, ties in storage order (a stable sort, done
  * by an on-device LSD radix sort).  mode = -1 builds all modes.  Unless
  * flags has SPT_PERM_INDEX_ONLY, the nonzeros are also copied in perm_n
- * order (a mode-sorted copy) so SPT_SCATTER_SORTED can stream them.
+ * order (a mode-sorted copy) so SPT_SCATTER_SORTED can stream them; with
+ * SPT_PERM_SLICE_ORDER each slice's nonzeros in the copy are ordered by the
+ * next modes (n+1, then n+2, cyclically; ties in storage order), so that
+ * neighbouring nonzeros of a long slice repeat factor rows and share their
+ * loads (two more radix sorts per mode).
  * Also records per-mode slice statistics used by the schedule selector.
  * Memory: 4P bytes per mode for perm_n, plus (4d + 4)P for the copy; the
  * radix sort borrows 16P bytes of temporary device memory. */
@@ -552,7 +557,9 @@ spt_status spt_fma_probe(spt_dtype dt, int64_t iters, double *sink, double *flop
  * the SMs and multiply them, by
  *   method 0: 16-byte global loads, 4 lanes per row (the MTTKRP kernel's way);
  *   method 1: TMA tile::gather4 into shared memory (four rows per instruction);
- *   method 2: one 1-D bulk copy per row into shared memory.
+ *   method 2: one 1-D bulk copy per row into shared memory;
+ *   method 3: as 0, with the 8 groups of a warp instruction on 8 consecutive
+ *             nonzeros (neighbours that repeat a row then share its load).
  * Enqueues one launch on `stream`; time it with events.  n a multiple of 64;
  * every pointer device, 16-byte aligned; sink a device float the kernel
  * never writes in practice; status a device int set to 1 if a bounded wait

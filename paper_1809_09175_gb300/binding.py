@@ -19,7 +19,7 @@ SPT_OK, SPT_EINVAL, SPT_ERANGE, SPT_ENOMEM, SPT_ECUDA = 0, 1, 2, 3, 4
 SPT_EUNSUPPORTED, SPT_ESINGULAR, SPT_ETIMEOUT, SPT_ESTATE = 5, 6, 7, 8
 SPT_F32, SPT_BF16, SPT_F16, SPT_F64 = 0, 1, 2, 3
 SPT_DEVICE_PTRS, SPT_COALESCE = 1, 2
-SPT_PERM_INDEX_ONLY = 1
+SPT_PERM_INDEX_ONLY, SPT_PERM_SLICE_ORDER = 1, 2
 SPT_SCATTER_AUTO, SPT_SCATTER_ATOMIC, SPT_SCATTER_PERM, SPT_SCATTER_SORTED, SPT_SCATTER_PRIVATE = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "SPT_OK", 1: "SPT_EINVAL", 2: "SPT_ERANGE", 3: "SPT_ENOMEM", 4: "SPT_ECUDA",

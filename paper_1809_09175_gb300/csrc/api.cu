@@ -265,12 +265,13 @@ spt_status tensor_norm2(spt_tensor t, double *out) {
 spt_status build_mode_permutation(spt_tensor t, int mode, int flags, void *stream) {
     if (!t) return fail(SPT_EINVAL, "build_mode_permutation: NULL tensor");
     if (mode < -1 || mode >= t->d) return fail(SPT_EINVAL, "build_mode_permutation: bad mode");
-    if (flags & ~SPT_PERM_INDEX_ONLY) return fail(SPT_EINVAL, "build_mode_permutation: unknown flag bits");
+    if (flags & ~(SPT_PERM_INDEX_ONLY | SPT_PERM_SLICE_ORDER))
+        return fail(SPT_EINVAL, "build_mode_permutation: unknown flag bits");
     cudaStream_t st = (cudaStream_t)stream;
     drop_graphs(t);
     for (int n = 0; n < t->d; ++n) {
         if (mode >= 0 && n != mode) continue;
-        spt_status s = build_perm_mode(t, n, (flags & SPT_PERM_INDEX_ONLY) != 0, st);
+        spt_status s = build_perm_mode(t, n, (flags & SPT_PERM_INDEX_ONLY) != 0, st, (flags & SPT_PERM_SLICE_ORDER) != 0);
         if (s) return s;
     }
     return SPT_OK;

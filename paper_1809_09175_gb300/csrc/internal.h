@@ -14,7 +14,7 @@ spt_status scan_exclusive(const int32_t *in, int32_t *out, int64_t n, int32_t *t
 spt_status radix_sort_pairs(const uint32_t *keys_in, const int32_t *vals_in, int64_t n, int bits,
                             uint32_t *keys_out, int32_t *vals_out, cudaStream_t st);
 spt_status coalesce_tensor(spt_tensor t, cudaStream_t st);
-spt_status build_perm_mode(spt_tensor t, int n, bool index_only, cudaStream_t st);
+spt_status build_perm_mode(spt_tensor t, int n, bool index_only, cudaStream_t st, bool slice_order = false);
 spt_status compute_norm2(spt_tensor t, cudaStream_t st);
 // The hot-row list of every mode (t->hot_buf, t->nhot); synchronises `st`.
 spt_status build_hot_rows(spt_tensor t, cudaStream_t st);

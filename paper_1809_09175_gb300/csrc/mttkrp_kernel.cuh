@@ -132,6 +132,11 @@ __device__ __forceinline__ void store4(double *dst, const double *v) {
     reinterpret_cast<double2 *>(dst)[1] = make_double2(v[2], v[3]);
 }
 
+// 0: every chunk takes the group-contiguous walk (build variant for comparisons)
+#ifndef SPT_SINGLE_ROW_CHUNKS
+#define SPT_SINGLE_ROW_CHUNKS 1
+#endif
+
 // Register cap: small column blocks fit two 512-thread CTAs (<= 64 registers).
 #ifndef SPT_MTTKRP_MINBLOCKS
 #define SPT_MTTKRP_MINBLOCKS 2
@@ -446,6 +451,64 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
             }
         };
 
+        const bool single_row = SPT_SINGLE_ROW_CHUNKS && MODE == M_SORTED && !GCP && !DET && carry && n == npw &&
+                                buf[0] == buf[(n - 1) * REC];
+#if SPT_SINGLE_ROW_CHUNKS
+        if (single_row) {
+            // A full chunk inside one row (a long slice): the groups take
+            // consecutive nonzeros (t*G + g), so factor rows that neighbours
+            // repeat -- the mode-sorted copy orders a slice by the other
+            // modes -- share one load in a warp instruction; then the
+            // groups' sums are added by a shuffle butterfly and join the run
+            // carried from the previous chunk.
+            for (int t = 0; t + U <= S; t += U) {
+                int rowu[U];
+                float xu[U];
+                Raw raw[U][NR][C];
+#pragma unroll
+                for (int u = 0; u < U; ++u) fetch((t + u) * G + g, rowu[u], xu[u], raw[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) step(rowu[u], xu[u], raw[u], true);
+            }
+            for (int t = S - S % U; t < S; ++t) {
+                int row;
+                float x;
+                Raw rw[NR][C];
+                fetch(t * G + g, row, x, rw);
+                step(row, x, rw, true);
+            }
+            for (int off = L; off < 32; off <<= 1)
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[c][v] += __shfl_xor_sync(FULL, acc[c][v], off);
+            int *crow_p = reinterpret_cast<int *>(carry);
+            AT *cacc_p = reinterpret_cast<AT *>(carry + 16) + l * (C * VEC);
+            const int crow = *crow_p;
+            AT cin[C][VEC];
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) cin[c][v] = cacc_p[c * VEC + v];
+            if (crow == cur) {
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[c][v] += cin[c][v];
+            } else if (crow >= 0 && g == 0) {  // the carried run ended before this chunk
+                write_row(crow, cin, crow == crow_p[1] || crow == crow_p[2], crow == crow_p[2]);
+            }
+            __syncwarp();  // every lane has read the carry
+            if (g == 0) {
+                if (l == 0) *crow_p = cur;
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) cacc_p[c * VEC + v] = acc[c][v];
+            }
+            continue;  // the only rank block
+        }
+#endif
         if (n == npw) {
             // full chunk: every group walks exactly S nonzeros, U at a time
             int t = 0;

@@ -8,7 +8,9 @@
 //   1  TMA cp.async.bulk.tensor tile::gather4 (four rows per instruction,
 //      2-D tensor map) into double-buffered shared memory, read back with
 //      16-byte shared loads;
-//   2  one 1-D cp.async.bulk per row into the same buffers.
+//   2  one 1-D cp.async.bulk per row into the same buffers;
+//   3  as 0, but the 8 groups of a warp instruction take 8 consecutive
+//      nonzeros (rows repeated among neighbours then share a load).
 // Each nonzero gathers one row of F1 (index r1[i]) and one of F2 (r2[i]) and
 // multiplies them, as the 3-way MTTKRP does; the products are kept live by a
 // store that never happens.
@@ -33,6 +35,9 @@ __device__ __forceinline__ void fma4(float4 &acc, const float4 &x, const float4 
     acc.w = fmaf(x.w, y.w, acc.w);
 }
 
+// INTERLEAVED: the 8 groups of a warp instruction take 8 consecutive
+// nonzeros (t * 8 + g) instead of 8 nonzeros a chunk's eighth apart
+template <bool INTERLEAVED>
 __global__ void __launch_bounds__(128) gather_ldg_kernel(const float *F1, const float *F2, const int32_t *r1,
                                                          const int32_t *r2, int64_t nchunk, float *sink) {
     const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
@@ -42,7 +47,7 @@ __global__ void __launch_bounds__(128) gather_ldg_kernel(const float *F1, const 
     for (int64_t ch = gw * nchunk / nw; ch < (gw + 1) * nchunk / nw; ++ch) {
 #pragma unroll 4
         for (int t = 0; t < GP_NPW / 8; ++t) {
-            const int64_t e = ch * GP_NPW + g * (GP_NPW / 8) + t;
+            const int64_t e = ch * GP_NPW + (INTERLEAVED ? t * 8 + g : g * (GP_NPW / 8) + t);
             const int a = __ldg(r1 + e), b = __ldg(r2 + e);
             fma4(acc, __ldg(reinterpret_cast<const float4 *>(F1 + (int64_t)a * 16) + l),
                  __ldg(reinterpret_cast<const float4 *>(F2 + (int64_t)b * 16) + l));
@@ -165,7 +170,7 @@ using namespace spt;
 extern "C" spt_status spt_row_gather_probe(int method, const float *F1, int64_t I1, const float *F2, int64_t I2,
                                            const int32_t *r1, const int32_t *r2, int64_t n, float *sink,
                                            int *status, void *stream) {
-    if (method < 0 || method > 2) return fail(SPT_EINVAL, "spt_row_gather_probe: method must be 0, 1 or 2");
+    if (method < 0 || method > 3) return fail(SPT_EINVAL, "spt_row_gather_probe: method must be 0..3");
     if (!F1 || !F2 || !r1 || !r2 || !sink || !status) return fail(SPT_EINVAL, "spt_row_gather_probe: NULL argument");
     if (I1 < 1 || I2 < 1 || I1 > INT32_MAX || I2 > INT32_MAX) return fail(SPT_EINVAL, "spt_row_gather_probe: bad row count");
     if (n < 0 || n % GP_NPW) return fail(SPT_EINVAL, "spt_row_gather_probe: n must be a multiple of 64");
@@ -175,9 +180,10 @@ extern "C" spt_status spt_row_gather_probe(int method, const float *F1, int64_t 
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nchunk = n / GP_NPW;
     int bps = 0;
-    if (method == 0) {
-        SPT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, gather_ldg_kernel, 32 * GP_WPC, 0));
-        gather_ldg_kernel<<<std::max(1, bps) * sm_count(), 32 * GP_WPC, 0, st>>>(F1, F2, r1, r2, nchunk, sink);
+    if (method == 0 || method == 3) {
+        auto kf = method == 0 ? gather_ldg_kernel<false> : gather_ldg_kernel<true>;
+        SPT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kf, 32 * GP_WPC, 0));
+        kf<<<std::max(1, bps) * sm_count(), 32 * GP_WPC, 0, st>>>(F1, F2, r1, r2, nchunk, sink);
         SPT_LAUNCH_CHECK("gather_ldg_kernel");
         return SPT_OK;
     }

@@ -440,7 +440,7 @@ spt_status coalesce_tensor(spt_tensor t, cudaStream_t st) {
 
 // Permutation of mode n (and the mode-sorted copy unless index_only), plus
 // slice statistics.  Synchronises `st` at the end.
-spt_status build_perm_mode(spt_tensor t, int n, bool index_only, cudaStream_t st) {
+spt_status build_perm_mode(spt_tensor t, int n, bool index_only, cudaStream_t st, bool slice_order) {
     const int64_t P = t->nnz;
     const int d = t->d;
     // release an earlier build of this mode
@@ -456,16 +456,47 @@ spt_status build_perm_mode(spt_tensor t, int n, bool index_only, cudaStream_t st
     if (s) { dfree(perm, st); dfree(srows, st); return s; }
     const int g = grid_for(P, 256);
     if (!index_only) {
+        // The copy's order: perm_n, or with slice_order by mode n and inside
+        // a slice by the next modes (n+1, then n+2, cyclically; ties in
+        // storage order), so that neighbouring nonzeros of a long slice
+        // repeat factor rows.  A stable LSD sort: mode n+2, then mode n+1,
+        // then mode n.
+        int32_t *ord = nullptr, *ord2 = nullptr;
+        uint32_t *kin = nullptr, *kout = nullptr;
+        const int nsec = slice_order ? std::min(2, d - 1) : 0;
+        if (nsec > 0 && P > 0) {
+            s = dmalloc((void **)&ord, seg_bytes(P, 4), st);
+            if (!s) s = dmalloc((void **)&ord2, seg_bytes(P, 4), st);
+            if (!s) s = dmalloc((void **)&kin, seg_bytes(P, 4), st);
+            if (!s) s = dmalloc((void **)&kout, seg_bytes(P, 4), st);
+            for (int q = nsec; q >= 0 && !s; --q) {
+                const int m = (n + q) % d;
+                const int mb = bit_width_u32((uint64_t)(t->dims[m] - 1));
+                if (q == nsec) {
+                    s = radix_sort_pairs(reinterpret_cast<const uint32_t *>(t->idx[m]), nullptr, P, mb, kout, ord,
+                                         st);
+                } else {
+                    gather_i32_kernel<<<g, 256, 0, st>>>(t->idx[m], ord, P, reinterpret_cast<int32_t *>(kin));
+                    s = radix_sort_pairs(kin, ord, P, mb, kout, ord2, st);
+                    std::swap(ord, ord2);
+                }
+            }
+        }
         const int rw = record_words(d);
         void *sbuf = nullptr;
-        s = dmalloc(&sbuf, seg_bytes(P * rw, 4), st);
-        if (s) { dfree(perm, st); dfree(srows, st); return s; }
+        if (!s) s = dmalloc(&sbuf, seg_bytes(P * rw, 4), st);
+        if (s) {
+            dfree(ord, st); dfree(ord2, st); dfree(kin, st); dfree(kout, st);
+            dfree(perm, st); dfree(srows, st);
+            return s;
+        }
         IdxPtrs ip;
         for (int m = 0; m < d; ++m) ip.p[m] = t->idx[m];
-        if (P > 0)
-            pack_records_kernel<<<g, 256, 0, st>>>(ip, d, n, t->vals, perm, srows, P, rw,
+        if (P > 0)  // the copy's mode-n keys equal srows: both orders sort by mode n first
+            pack_records_kernel<<<g, 256, 0, st>>>(ip, d, n, t->vals, ord ? ord : perm, srows, P, rw,
                                                    reinterpret_cast<int32_t *>(sbuf));
         SPT_LAUNCH_CHECK("pack_records_kernel");
+        dfree(ord, st); dfree(ord2, st); dfree(kin, st); dfree(kout, st);
         t->sorted_buf[n] = sbuf;
     }
     t->perm[n] = perm;

@@ -78,9 +78,11 @@ class SparseTensor:
         except Exception:
             pass
 
-    def build_permutation(self, mode: int = -1, index_only: bool = False):
-        B.build_mode_permutation(self.handle, mode, B.SPT_PERM_INDEX_ONLY if index_only else 0,
-                                 _stream())
+    def build_permutation(self, mode: int = -1, index_only: bool = False, slice_order: bool = False):
+        """perm_n and (unless index_only) the mode-sorted copy; slice_order
+        orders each slice of the copy by the next modes (SPT_PERM_SLICE_ORDER)."""
+        flags = (B.SPT_PERM_INDEX_ONLY if index_only else 0) | (B.SPT_PERM_SLICE_ORDER if slice_order else 0)
+        B.build_mode_permutation(self.handle, mode, flags, _stream())
 
     def permutation(self, mode: int) -> torch.Tensor:
         out = torch.empty(self.nnz, dtype=torch.int32, device="cuda")

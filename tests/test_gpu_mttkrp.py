@@ -344,3 +344,34 @@ def test_row_with_two_million_nonzeros(scatter, dist, R):
         assert err <= TOL["f32"], (n, err)
         if n == 0:  # the hot row by itself
             assert rel_fro(outs[n][7, :R], ref[7]) <= TOL["f32"], n
+
+
+@pytest.mark.parametrize("order", [3, 4, 5])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_slice_ordered_copy_and_single_row_chunks(order, dtype):
+    """Mode-sorted copies built with SPT_PERM_SLICE_ORDER (each slice ordered
+    by the next modes) and power-law rows long enough that whole chunks lie in
+    one row (those take the consecutive-nonzero walk): every mode against the
+    oracle, for several chunk shapes, and the deterministic call bit-identical
+    from call to call."""
+    P = _lib()
+    dims = {3: (400, 300, 200), 4: (300, 200, 100, 50), 5: (200, 150, 100, 50, 20)}[order]
+    R = 24
+    idx, vals = synth.coo_zipf(dims, 200_000, 1.3, 40 + order)
+    facs = synth.factor_matrices(dims, R, 40 + order, "normal", dtype=dtype)
+    T = P.SparseTensor(idx, vals, dims)
+    T.build_permutation(slice_order=True)
+    dev = [to_device_factor(f, dtype) for f in facs]
+    for n in range(order):
+        ref = _oracle(idx, vals, dims, facs, dtype, R, n)
+        for S_, lanes, warps in [(7, 8, 4), (23, 8, 8), (63, 4, 8)]:
+            sc = P.spt_schedule.make("sorted", lanes_per_nnz=lanes, chunks=1 if lanes * 4 >= R else 2,
+                                     nnz_per_group=S_, warps_per_cta=warps)
+            got = T.mttkrp(n, dev, R, sched=sc).cpu().numpy()[:, :R]
+            assert rel_fro(got, ref) <= TOL[dtype], (n, S_, lanes)
+        a = T.mttkrp(n, dev, R, deterministic=True).cpu().numpy()
+        b = T.mttkrp(n, dev, R, deterministic=True).cpu().numpy()
+        np.testing.assert_array_equal(a, b)
+        assert rel_fro(a[:, :R], ref) <= TOL[dtype]
+    T.check()
+    T.close()
