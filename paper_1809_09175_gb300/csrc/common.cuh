@@ -64,6 +64,13 @@ struct spt_tensor_s {
     // atomic scatter adds their row sums into shared memory (see mttkrp_kernel)
     int32_t *hot_buf = nullptr;  // SPT_HOT_MAX entries per mode
     int nhot[SPT_MAX_ORDER] = {0};
+    // nonzero counts of the listed rows and of the first row past the list
+    // (hot_count[n][k], k <= nhot[n]; 0 past the candidates)
+    int64_t hot_count[SPT_MAX_ORDER][SPT_HOT_MAX + 1] = {{0}};
+    // sums over the mode's rows of count^2 and count^3 (the atomic scatter's
+    // estimate of the rounding error of long fp32 chains of adds)
+    double cnt_s2[SPT_MAX_ORDER] = {0.0};
+    double cnt_s3[SPT_MAX_ORDER] = {0.0};
 };
 
 // ---- host error handling -------------------------------------------------

@@ -1,5 +1,6 @@
 // mttkrp_host.cu -- schedule logic and launch of the MTTKRP kernel.
 #include <atomic>
+#include <cmath>
 #include <mutex>
 #include <unordered_map>
 
@@ -10,6 +11,18 @@
 // (R = 16 fp32: 256 rows; R = 64: 64 rows).
 #ifndef SPT_HOT_SMEM
 #define SPT_HOT_SMEM (16 * 1024)
+#endif
+// Atomic scatter: the estimated relative error of the adds above which they
+// are split over copies of the output (a third of the 1e-5 fp32 gate), at
+// most SPT_ATOMIC_COPIES_MAX copies of at most SPT_ATOMIC_COPY_BYTES in all.
+#ifndef SPT_ATOMIC_COPY_EST
+#define SPT_ATOMIC_COPY_EST 3e-6
+#endif
+#ifndef SPT_ATOMIC_COPIES_MAX
+#define SPT_ATOMIC_COPIES_MAX 64
+#endif
+#ifndef SPT_ATOMIC_COPY_BYTES
+#define SPT_ATOMIC_COPY_BYTES (512ll << 20)
 #endif
 
 // 0: never take the clamped-gather kernels (build variant for comparisons)
@@ -125,6 +138,47 @@ spt_status launch_det(MttkrpKernelFn fn, MttkrpParams p, int blocks, int wpc, si
     }
     dfree(buf, st);
     if (e != cudaSuccess) return cuda_fail(e, "mttkrp deterministic launch");
+    return SPT_OK;
+}
+
+// out[i] = the sum of the nrep copies scratch[r * n + i] (fp64 sum, one rounding)
+template <typename AT>
+__global__ void sum_copies_kernel(const AT *__restrict__ scratch, int nrep, int64_t n, AT *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int r = 0; r < nrep; ++r) a += (double)scratch[(int64_t)r * n + i];
+        out[i] = (AT)a;
+    }
+}
+
+// Atomic scatter into nrep zeroed copies of the output (stream-ordered
+// scratch; CTA b adds into copy b mod nrep), summed into the output after.
+// Each copy takes 1/nrep of every row's adds, so each chain of fp32 adds is
+// nrep times shorter and its partial sums nrep times smaller.
+spt_status launch_copies(MttkrpKernelFn fn, MttkrpParams p, int blocks, int wpc, size_t smem, int64_t In, int ab,
+                         cudaStream_t st) {
+    const int64_t n = In * p.old;
+    void *buf = nullptr;
+    spt_status c = dmalloc(&buf, (size_t)ab * (size_t)n * p.nrep, st);
+    if (c) return c;
+    void *out = p.out;
+    p.out = buf;
+    p.rep_stride = n;
+    cudaError_t e = cudaMemsetAsync(buf, 0, (size_t)ab * (size_t)n * p.nrep, st);
+    if (e == cudaSuccess) {
+        fn<<<blocks, wpc * 32, smem, st>>>(p);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, sm_count() * 8));
+        if (ab == 8)
+            sum_copies_kernel<double><<<g, 256, 0, st>>>((const double *)buf, p.nrep, n, (double *)out);
+        else
+            sum_copies_kernel<float><<<g, 256, 0, st>>>((const float *)buf, p.nrep, n, (float *)out);
+        e = cudaGetLastError();
+    }
+    dfree(buf, st);
+    if (e != cudaSuccess) return cuda_fail(e, "mttkrp atomic scatter into copies");
     return SPT_OK;
 }
 
@@ -301,6 +355,29 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
             smem += hot_smem_bytes(nhot, pld, ab, p.hot_log2T);
         }
     }
+    // fp32 atomic adds drift along long chains: a row past the hot list takes
+    // one add per nonzero (count_k adds), a relative error of about
+    // 2^-24 sqrt(count_k) while the rounding errors stay random (more once
+    // the partial sums dwarf the terms), i.e. over the output about
+    //   2^-24 sqrt(sum_k count_k^3 / sum_all count^2)
+    // (rows weighted by their share of ||V||^2, nonnegative terms).  Twice
+    // that, above SPT_ATOMIC_COPY_EST, splits the adds over nrep copies of
+    // the output (error / nrep or better), as many as SPT_ATOMIC_COPY_BYTES
+    // and the grid allow.
+    p.nrep = 1;
+    p.rep_stride = 0;
+    if (kmode == M_ATOMIC && t->cnt_s2[mode] > 0.0) {
+        double s3 = t->cnt_s3[mode];
+        for (int q = 0; q < p.nhot; ++q) {
+            const double c = (double)t->hot_count[mode][q];
+            s3 -= c * c * c;
+        }
+        const double est = 2.0 * std::ldexp(1.0, ab == 4 ? -24 : -53) * std::sqrt(std::max(0.0, s3) / t->cnt_s2[mode]);
+        const double copy_bytes = (double)t->dims[mode] * p.old * ab;
+        while (p.nrep < SPT_ATOMIC_COPIES_MAX && est / p.nrep > SPT_ATOMIC_COPY_EST &&
+               copy_bytes * 2 * p.nrep <= (double)SPT_ATOMIC_COPY_BYTES)
+            p.nrep *= 2;
+    }
     int K = 1;
     if (kmode == M_PRIVATE) {
         const int log2K = private_cluster_log2(t->dims[mode], rank, smem, ab);
@@ -368,6 +445,10 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
     const int64_t need = (p.nchunks + wpc - 1) / wpc;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)cps * sm_count(), need));
     if (det) return launch_det(fn, p, blocks, wpc, smem, ab, st);
+    if (p.nrep > 1) {
+        while (p.nrep > 1 && p.nrep > blocks) p.nrep >>= 1;  // a copy per CTA at most
+        if (p.nrep > 1) return launch_copies(fn, p, blocks, wpc, smem, t->dims[mode], ab, st);
+    }
     fn<<<blocks, wpc * 32, smem, st>>>(p);
     SPT_LAUNCH_CHECK("mttkrp_kernel launch");
     return SPT_OK;

@@ -93,6 +93,9 @@ struct MttkrpParams {
     const int32_t *hot_rows;  // nhot row ids, hottest first
     int nhot;
     int hot_log2T;            // hash table of 1 << hot_log2T slots (>= 2 nhot)
+    int nrep;                 // M_ATOMIC: copies of the output (a power of two, >= 1); CTA b
+    int64_t rep_stride;       // adds into copy b & (nrep - 1), rep_stride elements apart
+                              // (out is then a scratch summed into the output afterwards)
     // M_PRIVATE: the private output copy in shared memory
     int In;       // rows of the output (mode length)
     int pld;      // row stride of the shared-memory copy (private or hot rows) in
@@ -290,6 +293,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
                 }
             }
             AT *dst = reinterpret_cast<AT *>(p.out) + (int64_t)row * p.old;
+            if (MODE == M_ATOMIC) dst += (int64_t)(blockIdx.x & (p.nrep - 1)) * p.rep_stride;
             if (DET && atomic && dslot >= 0) {  // deterministic: this warp's slot
                 const int slot = 2 * (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) + dslot;
                 dst = reinterpret_cast<AT *>(p.det_vals) + (int64_t)slot * p.old;
@@ -311,7 +315,9 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
         };
 
         // load one nonzero's row, value and its d-1 factor-row chunks
-        auto fetch = [&](int e, int &row, float &x, Raw (&rw)[NR][C]) {
+        // own_row = false: the generalised CP's own-factor row is not loaded
+        // (a single-row chunk loads it once for all its nonzeros)
+        auto fetch = [&](int e, int &row, float &x, Raw (&rw)[NR][C], bool own_row = true) {
             int r[DA];
             if (MODE == M_SORTED) {
                 int w[REC];
@@ -349,7 +355,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
                 for (int c = 0; c < C; ++c)
                     rw[m][c] = (CLAMP || nv[c] > 0) ? E::load(fb[m][c] + (int64_t)r[m] * rstride) : Raw{};
             }
-            if (GCP) {
+            if (GCP && own_row) {
 #pragma unroll
                 for (int c = 0; c < C; ++c)
                     rw[NR - 1][c] = (CLAMP || nv[c] > 0) ? E::load(fb[NR - 1][c] + (int64_t)row * rstride) : Raw{};
@@ -451,7 +457,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
             }
         };
 
-        const bool single_row = SPT_SINGLE_ROW_CHUNKS && MODE == M_SORTED && !GCP && !DET && carry && n == npw &&
+        const bool single_row = SPT_SINGLE_ROW_CHUNKS && MODE == M_SORTED && !DET && carry && n == npw &&
                                 buf[0] == buf[(n - 1) * REC];
 #if SPT_SINGLE_ROW_CHUNKS
         if (single_row) {
@@ -460,13 +466,26 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
             // repeat -- the mode-sorted copy orders a slice by the other
             // modes -- share one load in a warp instruction; then the
             // groups' sums are added by a shuffle butterfly and join the run
-            // carried from the previous chunk.
+            // carried from the previous chunk.  The generalised CP's own row
+            // is the same for every nonzero: loaded once.
+            Raw own[C];
+            if (GCP) {
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    own[c] = (CLAMP || nv[c] > 0) ? E::load(fb[NR - 1][c] + (int64_t)buf[0] * rstride) : Raw{};
+            }
             for (int t = 0; t + U <= S; t += U) {
                 int rowu[U];
                 float xu[U];
                 Raw raw[U][NR][C];
 #pragma unroll
-                for (int u = 0; u < U; ++u) fetch((t + u) * G + g, rowu[u], xu[u], raw[u]);
+                for (int u = 0; u < U; ++u) {
+                    fetch((t + u) * G + g, rowu[u], xu[u], raw[u], false);
+                    if (GCP) {
+#pragma unroll
+                        for (int c = 0; c < C; ++c) raw[u][NR - 1][c] = own[c];
+                    }
+                }
 #pragma unroll
                 for (int u = 0; u < U; ++u) step(rowu[u], xu[u], raw[u], true);
             }
@@ -474,9 +493,14 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
                 int row;
                 float x;
                 Raw rw[NR][C];
-                fetch(t * G + g, row, x, rw);
+                fetch(t * G + g, row, x, rw, false);
+                if (GCP) {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) rw[NR - 1][c] = own[c];
+                }
                 step(row, x, rw, true);
             }
+            if (GCP) *lacc += (double)lsum;  // the loss terms of the chunk's nonzeros
             for (int off = L; off < 32; off <<= 1)
 #pragma unroll
                 for (int c = 0; c < C; ++c)
@@ -1108,8 +1132,10 @@ __device__ __forceinline__ void mttkrp_atomic_hot(const MttkrpParams &p, unsigne
         const int slot = i / q4, c4 = i - slot * q4;
         const AT *src = hot + (int64_t)slot * p.pld + 4 * c4;
         const AT v[4] = {src[0], src[1], src[2], src[3]};
-        if (v[0] != (AT)0 || v[1] != (AT)0 || v[2] != (AT)0 || v[3] != (AT)0)
-            red_add4(reinterpret_cast<AT *>(p.out) + (int64_t)__ldg(p.hot_rows + slot) * p.old + 4 * c4, v);
+        if (v[0] == (AT)0 && v[1] == (AT)0 && v[2] == (AT)0 && v[3] == (AT)0) continue;
+        const int64_t o = (int64_t)__ldg(p.hot_rows + slot) * p.old + 4 * c4 +
+                          (int64_t)(blockIdx.x & (p.nrep - 1)) * p.rep_stride;
+        red_add4(reinterpret_cast<AT *>(p.out) + o, v);
     }
 }
 

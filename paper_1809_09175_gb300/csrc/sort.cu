@@ -551,6 +551,24 @@ __global__ void hot_flag_kernel(const int32_t *cnt, int64_t I, int32_t minc, int
         flag[r] = cnt[r] >= minc ? 1 : 0;
 }
 
+// s[0] += sum count^2, s[1] += sum count^3 over the rows
+__global__ void count_moments_kernel(const int32_t *cnt, int64_t I, double *s) {
+    double a = 0.0, b = 0.0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < I; r += (int64_t)gridDim.x * blockDim.x) {
+        const double c = (double)cnt[r];
+        a += c * c;
+        b += c * c * c;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(FULL, a, o);
+        b += __shfl_xor_sync(FULL, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(s, a);
+        atomicAdd(s + 1, b);
+    }
+}
+
 // candidates in row order: key = P - count (so an ascending sort puts the
 // hottest first), value = row
 __global__ void hot_compact_kernel(const int32_t *cnt, const int32_t *flag, const int32_t *pos, int64_t I,
@@ -572,34 +590,45 @@ spt_status build_hot_rows(spt_tensor t, cudaStream_t st) {
         spt_status s = dmalloc((void **)&t->hot_buf, sizeof(int32_t) * SPT_HOT_MAX * SPT_MAX_ORDER, st);
         if (s) return s;
     }
-    for (int n = 0; n < t->d; ++n) t->nhot[n] = 0;
+    for (int n = 0; n < t->d; ++n) {
+        t->nhot[n] = 0;
+        for (int k = 0; k <= SPT_HOT_MAX; ++k) t->hot_count[n][k] = 0;
+    }
     if (P < SPT_HOT_MIN_COUNT) return SPT_OK;
     for (int n = 0; n < t->d; ++n) {
         const int64_t I = t->dims[n];
         int32_t *cnt = nullptr, *flag = nullptr, *pos = nullptr, *total = nullptr, *rows = nullptr, *srows = nullptr;
         uint32_t *keys = nullptr, *skeys = nullptr;
+        double *mom = nullptr;
         auto cleanup = [&]() {
             dfree(cnt, st); dfree(flag, st); dfree(pos, st); dfree(total, st);
-            dfree(rows, st); dfree(srows, st); dfree(keys, st); dfree(skeys, st);
+            dfree(rows, st); dfree(srows, st); dfree(keys, st); dfree(skeys, st); dfree(mom, st);
         };
         spt_status s = dmalloc((void **)&cnt, 4 * I, st);
         if (!s) s = dmalloc((void **)&flag, 4 * I, st);
         if (!s) s = dmalloc((void **)&pos, 4 * I, st);
         if (!s) s = dmalloc((void **)&total, 4, st);
+        if (!s) s = dmalloc((void **)&mom, 2 * sizeof(double), st);
         if (s) { cleanup(); return s; }
         cudaError_t e = cudaMemsetAsync(cnt, 0, 4 * I, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(mom, 0, 2 * sizeof(double), st);
         if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "build_hot_rows memset"); }
         slice_count_kernel<<<grid_for(P, 256), 256, 0, st>>>(t->idx[n], P, cnt);
         hot_flag_kernel<<<grid_for(I, 256), 256, 0, st>>>(cnt, I, SPT_HOT_MIN_COUNT, flag);
+        count_moments_kernel<<<grid_for(I, 256), 256, 0, st>>>(cnt, I, mom);
         e = cudaGetLastError();
         if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "build_hot_rows kernels"); }
         s = scan_exclusive(flag, pos, I, total, st);
         int32_t nc = 0;
+        double hm[2] = {0.0, 0.0};
         if (!s) {
             e = cudaMemcpyAsync(&nc, total, 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hm, mom, sizeof(hm), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) s = cuda_fail(e, "build_hot_rows count");
         }
+        t->cnt_s2[n] = hm[0];
+        t->cnt_s3[n] = hm[1];
         if (!s && nc > 0) {
             s = dmalloc((void **)&keys, 4 * (size_t)nc, st);
             if (!s) s = dmalloc((void **)&rows, 4 * (size_t)nc, st);
@@ -612,12 +641,19 @@ spt_status build_hot_rows(spt_tensor t, cudaStream_t st) {
             }
             if (!s) s = radix_sort_pairs(keys, rows, nc, bit_width_u32((uint64_t)P), skeys, srows, st);
             const int k = std::min<int32_t>(nc, SPT_HOT_MAX);
+            uint32_t hk[SPT_HOT_MAX + 1];
+            const int kc = std::min<int32_t>(nc, SPT_HOT_MAX + 1);
             if (!s) {
                 e = cudaMemcpyAsync(t->hot_buf + (size_t)n * SPT_HOT_MAX, srows, 4 * (size_t)k,
                                     cudaMemcpyDeviceToDevice, st);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(hk, skeys, 4 * (size_t)kc, cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
                 if (e != cudaSuccess) s = cuda_fail(e, "build_hot_rows copy");
             }
-            if (!s) t->nhot[n] = k;
+            if (!s) {
+                t->nhot[n] = k;
+                for (int q = 0; q < kc; ++q) t->hot_count[n][q] = (int64_t)P - (int64_t)hk[q];
+            }
         }
         cleanup();
         if (s) return s;
