@@ -391,6 +391,15 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
         p.prows = (int)((t->dims[mode] + K - 1) / K);
         smem += (size_t)p.prows * p.pld * ab;
     }
+    // A private copy takes every add of its cluster's nonzeros to a row in
+    // one chain (count_k / clusters adds, the same fp32 drift as the atomic
+    // scatter's): waves of more clusters than fit at once, each over fewer
+    // nonzeros, shorten those chains, the estimate over the resident
+    // clusters above SPT_ATOMIC_COPY_EST doubling the waves (at most 64).
+    int waves = 1;
+    double priv_est = 0.0;
+    if (kmode == M_PRIVATE && t->cnt_s2[mode] > 0.0)
+        priv_est = 2.0 * std::ldexp(1.0, ab == 4 ? -24 : -53) * std::sqrt(t->cnt_s3[mode] / t->cnt_s2[mode]);
     // a lane whose whole chunk lies past column R: with at most 8 lanes per
     // nonzero the sorted traversal takes the clamped-gather kernels, whose
     // gathers then do not diverge (measured: 4-way R=20 1.55x, 5-way R=20
@@ -432,7 +441,9 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
         SPT_CUDA(cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg));
         if (ncl < 1) return fail(SPT_EINVAL, "schedule: a cluster of the private scatter does not fit the GPU");
         const int64_t need_cl = ((p.nchunks + wpc - 1) / wpc + K - 1) / K;
-        const int cl = (int)std::max<int64_t>(1, std::min<int64_t>(ncl, need_cl));
+        while (waves < 64 && priv_est / ((double)ncl * waves) > SPT_ATOMIC_COPY_EST && (int64_t)ncl * waves < need_cl)
+            waves *= 2;
+        const int cl = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ncl * waves, need_cl));
         cfg.gridDim = dim3(cl * K);
         SPT_CUDA(cudaLaunchKernelEx(&cfg, fn, p));
         SPT_LAUNCH_CHECK("mttkrp_kernel cluster launch");
@@ -443,7 +454,10 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
     if (bps < 1) return fail(SPT_EINVAL, "schedule: kernel does not fit on an SM");
     const int cps = s.ctas_per_sm > 0 ? std::min(s.ctas_per_sm, bps) : bps;
     const int64_t need = (p.nchunks + wpc - 1) / wpc;
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)cps * sm_count(), need));
+    while (waves < 64 && priv_est / ((double)cps * sm_count() * waves) > SPT_ATOMIC_COPY_EST &&
+           (int64_t)cps * sm_count() * waves < need)
+        waves *= 2;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)cps * sm_count() * waves, need));
     if (det) return launch_det(fn, p, blocks, wpc, smem, ab, st);
     if (p.nrep > 1) {
         while (p.nrep > 1 && p.nrep > blocks) p.nrep >>= 1;  // a copy per CTA at most

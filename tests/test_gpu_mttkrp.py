@@ -346,6 +346,25 @@ def test_row_with_two_million_nonzeros(scatter, dist, R):
             assert rel_fro(outs[n][7, :R], ref[7]) <= TOL["f32"], n
 
 
+@pytest.mark.parametrize("scatter", ["private", "atomic"])
+def test_clustered_private_copy_with_a_row_of_six_million_nonzeros(scatter):
+    """A 20000-row mode at R = 16 (a 1.28 MB private copy: clusters of 8
+    CTAs, about 19 resident at once) whose row 7 holds 6e6 of 2e7 nonzeros in
+    random storage order.  One resident wave would add ~3e5 values into that
+    row of each cluster's copy; the private scatter runs more, shorter waves
+    of clusters instead and must stay within the fp32 gate, and so must the
+    atomic scatter (hot-row copy in shared memory)."""
+    P = _lib()
+    dims = (20_000, 3000, 2000)
+    R = 16
+    idx, vals = _hot_row_tensor(dims, 20_000_000, 6_000_000, 41)
+    facs = synth.factor_matrices(dims, R, 41, "uniform")
+    outs = _run(P, idx, vals, dims, facs, "f32", R, scatter, modes=[0])
+    ref = _oracle(idx, vals, dims, facs, "f32", R, 0)
+    assert rel_fro(outs[0][:, :R], ref) <= TOL["f32"]
+    assert rel_fro(outs[0][7, :R], ref[7]) <= TOL["f32"]
+
+
 @pytest.mark.parametrize("order", [3, 4, 5])
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_slice_ordered_copy_and_single_row_chunks(order, dtype):
