@@ -73,7 +73,6 @@ spt_status free_tensor_buffers(spt_tensor t) {
     for (int n = 0; n < SPT_MAX_ORDER; ++n) {
         dfree(t->perm[n], st);
         dfree(t->sorted_buf[n], st);
-        dfree(t->nz_bits[n], st);
     }
     dfree(t->coo_buf, st);
     dfree(t->dev_err, st);

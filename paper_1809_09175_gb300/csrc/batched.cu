@@ -28,75 +28,20 @@ struct BatchTask {
     int d1;               // order - 1 of the tensor
 };
 
-// One output of the batch: rows x ld floats (ld % 8 == 0).  Where `bits`
-// is set, the task's kernel stores the first keep4 quads of every row that
-// holds a nonzero, except the first and last row of each block (those take
-// atomic adds and are listed in the batch's row table): the zero-fill skips
-// those quads.
 struct ZeroSeg {
     float *ptr;
-    int64_t rows;
-    int ld4;                  // quads per row
-    int keep4;                // quads the kernel stores in a non-empty row
-    const uint32_t *bits;     // the mode's non-empty rows, or null: zero every quad
+    int64_t n;
 };
 
-// A row that takes atomic adds: ld4 quads at ptr.
-struct ZeroRow {
-    float *ptr;
-    int64_t ld4;
-};
-
-__global__ void batch_zero_kernel(const ZeroSeg *segs, int nseg, const ZeroRow *rows, int64_t nrows,
-                                  unsigned long long *counters, int ncnt) {
+__global__ void batch_zero_kernel(const ZeroSeg *segs, int nseg, unsigned long long *counters, int ncnt) {
     if (blockIdx.x == 0 && blockIdx.y == 0)
         for (int c = threadIdx.x; c < ncnt; c += blockDim.x) counters[c] = 0ull;
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int s = blockIdx.y; s < nseg; s += gridDim.y) {
-        const ZeroSeg sg = segs[s];
-        float4 *p4 = reinterpret_cast<float4 *>(sg.ptr);
-        const int64_t n4 = sg.rows * sg.ld4;
-        // quad i = (row, q) advanced by the grid stride without a division per quad
-        const int64_t sd = stride / sg.ld4;
-        const int sm = (int)(stride - sd * sg.ld4);
-        int64_t row = tid / sg.ld4;
-        int q = (int)(tid - row * sg.ld4);
-        for (int64_t i = tid; i < n4; i += stride) {
-            if (!(q < sg.keep4 && sg.bits && ((__ldg(sg.bits + (row >> 5)) >> (row & 31)) & 1u))) p4[i] = z;
-            row += sd;
-            q += sm;
-            if (q >= sg.ld4) {
-                q -= sg.ld4;
-                ++row;
-            }
-        }
-    }
-    // the listed rows: a warp per row over the whole grid
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.y * gridDim.x * (blockDim.x >> 5);
-    for (int64_t r = gw; r < nrows; r += nwarps) {
-        const ZeroRow zr = rows[r];
-        float4 *p4 = reinterpret_cast<float4 *>(zr.ptr);
-        for (int64_t q = lane; q < zr.ld4; q += 32) p4[q] = z;
-    }
-}
-
-// The rows of task blocks [0, nblocks) that take atomic adds: for block b,
-// the rows of its first and last nonzero (mode-sorted records, REC words
-// each, the row first) -> out[2b], out[2b + 1].
-__global__ void block_rows_kernel(const int32_t *rec, int rec_words, int64_t npw, int64_t nchunks, int64_t nnz,
-                                  int64_t nblocks, float *o, int ld, ZeroRow *out) {
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblocks; b += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c0 = b * BATCH_BLOCK_CHUNKS;
-        const int64_t c1 = c0 + BATCH_BLOCK_CHUNKS < nchunks ? c0 + BATCH_BLOCK_CHUNKS : nchunks;
-        const int64_t e0 = c0 * npw;
-        const int64_t e1 = (c1 * npw < nnz ? c1 * npw : nnz) - 1;
-        const int64_t r0 = rec[e0 * rec_words], r1 = rec[e1 * rec_words];
-        out[2 * b] = ZeroRow{o + r0 * ld, ld / 4};
-        out[2 * b + 1] = ZeroRow{o + r1 * ld, ld / 4};
+        float4 *p4 = reinterpret_cast<float4 *>(segs[s].ptr);
+        const int64_t n4 = segs[s].n / 4;  // outputs are I x ld with ld % 8 == 0
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+             i += (int64_t)gridDim.x * blockDim.x)
+            p4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -195,8 +140,6 @@ struct spt_batch_s {
     std::vector<BatchClass> classes;
     std::vector<ZeroSeg> hsegs;
     ZeroSeg *dsegs = nullptr;
-    ZeroRow *zrows = nullptr;  // rows that take atomic adds (zeroed every run)
-    int64_t nzrows = 0;
     unsigned long long *counters = nullptr;  // one per class
     int *err = nullptr;
     int64_t ntasks = 0;
@@ -207,10 +150,9 @@ struct spt_batch_s {
 
 namespace {
 spt_status enqueue_batch(spt_batch b, cudaStream_t st) {
-    if (b->classes.empty()) return SPT_OK;
+    if (b->hsegs.empty()) return SPT_OK;
     dim3 zg(64, (unsigned)std::max<size_t>(1, std::min<size_t>(b->hsegs.size(), 1024)));
-    batch_zero_kernel<<<zg, 256, 0, st>>>(b->dsegs, (int)b->hsegs.size(), b->zrows, b->nzrows, b->counters,
-                                          (int)b->classes.size());
+    batch_zero_kernel<<<zg, 256, 0, st>>>(b->dsegs, (int)b->hsegs.size(), b->counters, (int)b->classes.size());
     SPT_LAUNCH_CHECK("batch_zero_kernel");
     for (size_t c = 0; c < b->classes.size(); ++c) {
         BatchClass &k = b->classes[c];
@@ -228,7 +170,6 @@ spt_status enqueue_batch(spt_batch b, cudaStream_t st) {
 void free_batch(spt_batch b) {
     for (auto &k : b->classes) cudaFree(k.dtasks);
     cudaFree(b->dsegs);
-    cudaFree(b->zrows);
     cudaFree(b->counters);
     cudaFree(b->err);
     delete b;
@@ -246,14 +187,6 @@ spt_status mttkrp_batch_create(int count, const spt_batch_item *items, spt_dtype
     spt_batch b = new (std::nothrow) spt_batch_s();
     if (!b) return fail(SPT_ENOMEM, "mttkrp_batch_create: host allocation");
     b->fdt = fdt;
-    struct RowJob {
-        const int32_t *rec;
-        int rec_words;
-        int64_t npw, nchunks, nnz;
-        float *o;
-        int ld;
-    };
-    std::vector<RowJob> rowjobs;
     for (int q = 0; q < count; ++q) {
         const spt_batch_item &it = items[q];
         spt_tensor t = it.tensor;
@@ -317,15 +250,9 @@ spt_status mttkrp_batch_create(int count, const spt_batch_item *items, spt_dtype
             p.npw = G * S;
             p.nchunks = (t->nnz + p.npw - 1) / p.npw;
             p.loss = -1;
-            // one rank block: every row inside a block is stored whole (its
-            // first ceil(R/4) quads), so only empty rows, padding quads and
-            // the blocks' first and last rows need zeros
-            const bool skip = t->nz_bits[n] && t->nnz > 0 && p.n_rb == 1;
-            b->hsegs.push_back(ZeroSeg{o, t->dims[n], it.ld / 4, skip ? (it.rank + 3) / 4 : 0,
-                                       skip ? t->nz_bits[n] : nullptr});
+            b->hsegs.push_back(ZeroSeg{o, t->dims[n] * (int64_t)it.ld});
             ++b->ntasks;
             if (t->nnz == 0) continue;  // zero-filled, nothing to add
-            if (skip) rowjobs.push_back(RowJob{p.rec, record_words(t->d), p.npw, p.nchunks, t->nnz, o, it.ld});
             tk.d1 = t->d - 1;
             const bool o5 = t->d == 5;
             BatchClass *cls = nullptr;
@@ -351,18 +278,6 @@ spt_status mttkrp_batch_create(int count, const spt_batch_item *items, spt_dtype
     if (e == cudaSuccess) e = cudaMalloc(&b->dsegs, sizeof(ZeroSeg) * std::max<size_t>(1, b->hsegs.size()));
     if (e == cudaSuccess && !b->hsegs.empty())
         e = cudaMemcpy(b->dsegs, b->hsegs.data(), sizeof(ZeroSeg) * b->hsegs.size(), cudaMemcpyHostToDevice);
-    for (const RowJob &j : rowjobs) b->nzrows += 2 * ((j.nchunks + BATCH_BLOCK_CHUNKS - 1) / BATCH_BLOCK_CHUNKS);
-    if (e == cudaSuccess) e = cudaMalloc(&b->zrows, sizeof(ZeroRow) * std::max<int64_t>(1, b->nzrows));
-    int64_t zoff = 0;
-    for (const RowJob &j : rowjobs) {
-        if (e != cudaSuccess) break;
-        const int64_t nb = (j.nchunks + BATCH_BLOCK_CHUNKS - 1) / BATCH_BLOCK_CHUNKS;
-        const int g = (int)std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, 4096));
-        block_rows_kernel<<<g, 256>>>(j.rec, j.rec_words, j.npw, j.nchunks, j.nnz, nb, j.o, j.ld, b->zrows + zoff);
-        e = cudaGetLastError();
-        zoff += 2 * nb;
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     for (auto &k : b->classes) {
         if (e != cudaSuccess) break;
         k.stage_words = (k.stage_words + 3) & ~3;  // 16-byte aligned staging buffers

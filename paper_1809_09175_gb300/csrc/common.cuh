@@ -71,10 +71,6 @@ struct spt_tensor_s {
     // estimate of the rounding error of long fp32 chains of adds)
     double cnt_s2[SPT_MAX_ORDER] = {0.0};
     double cnt_s3[SPT_MAX_ORDER] = {0.0};
-    // per mode: bit r of word r / 32 set iff row r holds a nonzero (null for
-    // tensors under SPT_HOT_MIN_COUNT nonzeros); the batch's zero-fill skips
-    // the rows its kernels overwrite
-    uint32_t *nz_bits[SPT_MAX_ORDER] = {nullptr};
 };
 
 // ---- host error handling -------------------------------------------------

@@ -551,18 +551,6 @@ __global__ void hot_flag_kernel(const int32_t *cnt, int64_t I, int32_t minc, int
         flag[r] = cnt[r] >= minc ? 1 : 0;
 }
 
-// bits[w] bit j = (cnt[32 w + j] > 0): one warp per word
-__global__ void nz_bits_kernel(const int32_t *cnt, int64_t I, uint32_t *bits) {
-    const int64_t nw = (I + 31) / 32;
-    const int lane = threadIdx.x & 31;
-    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < nw;
-         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const int64_t r = w * 32 + lane;
-        const unsigned b = __ballot_sync(FULL, r < I && cnt[r] > 0);
-        if (lane == 0) bits[w] = b;
-    }
-}
-
 // s[0] += sum count^2, s[1] += sum count^3 over the rows
 __global__ void count_moments_kernel(const int32_t *cnt, int64_t I, double *s) {
     double a = 0.0, b = 0.0;
@@ -629,11 +617,6 @@ spt_status build_hot_rows(spt_tensor t, cudaStream_t st) {
         slice_count_kernel<<<grid_for(P, 256), 256, 0, st>>>(t->idx[n], P, cnt);
         hot_flag_kernel<<<grid_for(I, 256), 256, 0, st>>>(cnt, I, SPT_HOT_MIN_COUNT, flag);
         count_moments_kernel<<<grid_for(I, 256), 256, 0, st>>>(cnt, I, mom);
-        if (!t->nz_bits[n]) {
-            s = dmalloc((void **)&t->nz_bits[n], 4 * ((I + 31) / 32), st);
-            if (s) { cleanup(); return s; }
-        }
-        nz_bits_kernel<<<grid_for(32 * ((I + 31) / 32), 256), 256, 0, st>>>(cnt, I, t->nz_bits[n]);
         e = cudaGetLastError();
         if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "build_hot_rows kernels"); }
         s = scan_exclusive(flag, pos, I, total, st);

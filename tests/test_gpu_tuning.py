@@ -214,11 +214,12 @@ def test_batched_mixed_kernel_classes():
     """One batch whose tasks fall into several kernel classes (orders 3 and
     4, one and two chunks per lane via R = 136) and blocks of chunks that
     split tasks unevenly; R = 20 leaves a padding quad (ld = 24) in every
-    row, which the zero-fill must clear in rows the kernel stores; outputs
-    start non-zero.  Results against the oracle."""
+    row, which the zero-fill must clear in rows the kernel stores, and a
+    tensor without nonzeros must come out zero; outputs start non-zero.
+    Results against the oracle."""
     P = _lib()
     cases = [((700, 300, 90), 20_003, 136), ((500, 60, 40, 9), 30_011, 24), ((900, 800, 700), 7, 16),
-             ((3000, 200, 50), 40_009, 20)]
+             ((3000, 200, 50), 40_009, 20), ((60, 50, 40), 0, 16)]
     tensors, items, facs_all, outs_all, host = [], [], [], [], []
     for q, (dims, nnz, R) in enumerate(cases):
         idx, vals = synth.coo_zipf(dims, nnz, 1.1, 60 + q)
