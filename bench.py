@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="skip the variants / CP-ALS extras")
     ap.add_argument("--slice-order", type=int, default=1,
                     help="1: build the mode-sorted copies with each slice ordered by the next modes")
+    ap.add_argument("--l2-blocks", choices=["auto", "off"], default="auto",
+                    help="auto: give a mode an L2-blocked copy where its largest other factor exceeds "
+                         "twice --l2-block-mb (blocks of that many MB of the factor's rows)")
+    ap.add_argument("--l2-block-mb", type=float, default=48.0)
     ap.add_argument("--full-parity-s", type=float, default=120.0,
                     help="whole-output parity against the all-core oracle when its estimated time "
                          "is within this many seconds (0: off)")
@@ -146,6 +150,26 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def l2_block_plan(args, dims, ld, s_f):
+    """{mode: rows per block} for the modes whose largest other factor is
+    more than twice the block budget (--l2-blocks auto)."""
+    if args.l2_blocks == "off":
+        return {}
+    budget = args.l2_block_mb * 2 ** 20
+    plan = {}
+    for n in range(len(dims)):
+        m = max((k for k in range(len(dims)) if k != n), key=lambda k: dims[k])
+        if dims[m] * ld * s_f > 2 * budget:
+            plan[n] = max(1, int(budget // (ld * s_f)))
+    return plan
+
+
+def build_l2_blocks(T, plan):
+    for n, rows in plan.items():
+        T.build_l2_blocks(n, -1, rows)
+    return {str(n): list(T.l2_blocks(n)) for n in plan}
 
 
 def kernel_traffic(nnz):
@@ -300,6 +324,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_perm = time.perf_counter()
     T.build_permutation(-1, index_only=(args.scatter == "perm"), slice_order=bool(args.slice_order))
+    plan = l2_block_plan(args, w.dims, ld, s_f) if args.scatter == "sorted" else {}
+    l2_blocks = build_l2_blocks(T, plan)
     torch.cuda.synchronize()
     t_done = time.perf_counter()
     ingest_s, perm_s = t_perm - t_ing, t_done - t_perm
@@ -488,6 +514,7 @@ def run_ours(args):
                    "exhaustive autotune per mode (untimed set-up, %.1f s)" % tune_s,
                    "step": "MTTKRP of every mode (one launch per mode)",
                    "slice_order": bool(args.slice_order),
+                   "l2_blocks": l2_blocks or "none",
                    "l2": "inputs larger than L2 (COO stream "
                    f"{w.nnz * 4 * (d + 1) / 1e9:.1f} GB per mode pass)"},
         "per_mode_ms": mode_ms,
@@ -669,6 +696,7 @@ def measure_extras(args, P, torch, w, T, idx, vals, facs_np, dtype, R, d, ld, ou
     Tc = P.SparseTensor(idx, vals, w.dims, coalesce=True)
     t0 = time.perf_counter()
     Tc.build_permutation()  # plain copies: over a few iterations the slice order's longer build does not pay
+    build_l2_blocks(Tc, l2_block_plan(args, w.dims, ld, 4 if dtype == "f32" else 2))
     torch.cuda.synchronize()
     sort_s = time.perf_counter() - t0
     fc = [_dev_factor(torch, f, dtype) for f in facs_np]
@@ -727,6 +755,7 @@ def run_cpals(args):
     t_ingest = time.perf_counter() - t0
     t0 = time.perf_counter()
     T.build_permutation()
+    l2_blocks = build_l2_blocks(T, l2_block_plan(args, w.dims, ld, 4 if fdt == "f32" else 2))
     torch.cuda.synchronize()
     t_perm = time.perf_counter() - t0
     facs_np = w.factors(R, fdt)
@@ -813,7 +842,8 @@ def run_cpals(args):
         del ws, f
     line = {"metric": METRIC, "workload": w.name, "dims": w.dims, "nnz_generated": w.nnz,
             "nnz_coalesced": T.nnz, "R": R, "factors": fdt, "iterations": args.cpals,
-            "ingest_coalesce_s": t_ingest, "permutation_s": t_perm, "autotune_s": t_tune,
+            "ingest_coalesce_s": t_ingest, "permutation_s": t_perm, "l2_blocks": l2_blocks or "none",
+            "autotune_s": t_tune,
             "select_s": t_select, "autotune_best_ms_per_mode": auto_ms, "selector_detail": sel_info,
             "cp_als": res,
             "schedules": {k: [s_.as_dict() for s_ in v] for k, v in scheds.items()}}

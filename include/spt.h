@@ -156,6 +156,32 @@ spt_status tensor_check(spt_tensor t, void *stream);
  * radix sort borrows 16P bytes of temporary device memory. */
 spt_status build_mode_permutation(spt_tensor t, int mode, int flags, void *stream);
 
+/* Rows per block of build_mode_l2_blocks when block_rows < 0: 48 MB of
+ * factor rows at 256 bytes a row (R = 64 in fp32), about a third of L2. */
+#define SPT_L2_BLOCK_ROWS_DEFAULT 196608
+
+/* Build the L2-blocked copy of mode `mode`'s sorted records: the records of
+ * the mode-sorted copy grouped by blocks of `block_rows` consecutive rows of
+ * mode `blocked_mode` (-1: the other mode with the most rows; block_rows < 0:
+ * SPT_L2_BLOCK_ROWS_DEFAULT), each group keeping the copy's order (by mode
+ * `mode`, then its slice order) and padded with zero-valued copies of its
+ * last record to a multiple of 4 records.  While it exists, the sorted
+ * traversal of that mode (mttkrp, its autotuning and CP-ALS; not the
+ * deterministic, generalised-CP or batched calls, which keep the plain copy)
+ * runs one launch per group, adding the rows it owns into the output, so the
+ * gathers of the blocked mode's factor stay within one block at a time --
+ * where that factor is much larger than L2, its rows are then read from DRAM
+ * about once instead of once per nonzero.  block_rows == 0 drops the copy;
+ * rebuilding the mode's permutation drops it too.  Needs the mode-sorted
+ * copy (SPT_ESTATE otherwise).  Memory: the copy's size again plus 16 bytes
+ * per group.  Synchronises `stream`.  Errors: SPT_EINVAL for a bad mode, a
+ * blocked mode equal to `mode`, or more than 65536 blocks. */
+spt_status build_mode_l2_blocks(spt_tensor t, int mode, int blocked_mode, int64_t block_rows, void *stream);
+
+/* The L2-blocked copy of `mode`: blocked mode (-1 when there is none), rows
+ * per block and number of groups.  Host outputs, each nullable. */
+spt_status tensor_l2_blocks(spt_tensor t, int mode, int *blocked_mode, int64_t *block_rows, int64_t *groups);
+
 /* A new tensor holding the nonzeros at positions [begin, end) of the mode-n
  * permutation of t (perm_n order: increasing mode-n coordinate), with t's
  * dims: the piece of t one process or GPU owns when the nonzeros are split

@@ -159,6 +159,8 @@ _try_sig("mttkrp_batch_destroy", _vp)
 _try_sig("spt_set_wait_tries", C.c_int64)
 _try_sig("spt_row_gather_probe", C.c_int, _vp, C.c_int64, _vp, C.c_int64, _vp, _vp, C.c_int64, _vp, _vp, _vp)
 _try_sig("tensor_create_shard", _vp, C.c_int, C.c_int64, C.c_int64, _vp, C.POINTER(_vp))
+_try_sig("build_mode_l2_blocks", _vp, C.c_int, C.c_int, C.c_int64, _vp)
+_try_sig("tensor_l2_blocks", _vp, C.c_int, C.POINTER(C.c_int), _i64p, _i64p)
 _try_sig("cp_als_hinv", _vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp)
 _try_sig("cp_als_apply", _vp, C.c_int64, C.c_int, C.c_int, _vp, _vp, _vp, _vp)
 _try_sig("cp_als_normalize", _vp, _vp, C.c_int64, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp, _vp, _vp)
@@ -320,6 +322,20 @@ def cp_als_step(t: int, factor_ptrs: Sequence[int], fdt, rank: int, ld: int, lam
 
 def cp_als_status(workspace_ptr: int, stream: int = 0):
     _chk(_L.cp_als_status(workspace_ptr, stream or None))
+
+
+SPT_L2_BLOCK_ROWS_DEFAULT = 196608
+
+
+def build_mode_l2_blocks(t: int, mode: int, blocked_mode: int = -1, block_rows: int = -1, stream: int = 0):
+    _chk(_L.build_mode_l2_blocks(t, mode, blocked_mode, block_rows, stream or None))
+
+
+def tensor_l2_blocks(t: int, mode: int):
+    """(blocked mode or -1, rows per block, groups) of the mode's L2-blocked copy."""
+    bm, rows, groups = C.c_int(), C.c_int64(), C.c_int64()
+    _chk(_L.tensor_l2_blocks(t, mode, C.byref(bm), C.byref(rows), C.byref(groups)))
+    return bm.value, rows.value, groups.value
 
 
 def tensor_create_shard(t: int, mode: int, begin: int, end: int, stream: int = 0) -> int:

@@ -73,6 +73,7 @@ spt_status free_tensor_buffers(spt_tensor t) {
     for (int n = 0; n < SPT_MAX_ORDER; ++n) {
         dfree(t->perm[n], st);
         dfree(t->sorted_buf[n], st);
+        dfree(t->blk_buf[n], st);
     }
     dfree(t->coo_buf, st);
     dfree(t->dev_err, st);
@@ -274,6 +275,44 @@ spt_status build_mode_permutation(spt_tensor t, int mode, int flags, void *strea
         spt_status s = build_perm_mode(t, n, (flags & SPT_PERM_INDEX_ONLY) != 0, st, (flags & SPT_PERM_SLICE_ORDER) != 0);
         if (s) return s;
     }
+    return SPT_OK;
+}
+
+spt_status build_mode_l2_blocks(spt_tensor t, int mode, int blocked_mode, int64_t block_rows, void *stream) {
+    if (!t) return fail(SPT_EINVAL, "build_mode_l2_blocks: NULL tensor");
+    if (mode < 0 || mode >= t->d) return fail(SPT_EINVAL, "build_mode_l2_blocks: bad mode");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (block_rows == 0) {  // drop
+        drop_graphs(t);
+        if (t->blk_buf[mode]) dfree(t->blk_buf[mode], st);
+        t->blk_buf[mode] = nullptr;
+        t->blk_off[mode].clear();
+        t->blk_mode[mode] = -1;
+        t->blk_rows[mode] = 0;
+        SPT_CUDA(cudaStreamSynchronize(st));
+        return SPT_OK;
+    }
+    if (!t->sorted_buf[mode])
+        return fail(SPT_ESTATE, "build_mode_l2_blocks: needs the mode-sorted copy (build_mode_permutation)");
+    int bm = blocked_mode;
+    if (bm == -1) {
+        for (int m = 0; m < t->d; ++m)
+            if (m != mode && (bm < 0 || t->dims[m] > t->dims[bm])) bm = m;
+    }
+    if (bm < 0 || bm >= t->d || bm == mode) return fail(SPT_EINVAL, "build_mode_l2_blocks: bad blocked mode");
+    const int64_t rows = block_rows < 0 ? SPT_L2_BLOCK_ROWS_DEFAULT : block_rows;
+    if ((t->dims[bm] + rows - 1) / rows > 65536)
+        return fail(SPT_EINVAL, "build_mode_l2_blocks: more than 65536 blocks");
+    drop_graphs(t);
+    return build_l2_blocks(t, mode, bm, rows, st);
+}
+
+spt_status tensor_l2_blocks(spt_tensor t, int mode, int *blocked_mode, int64_t *block_rows, int64_t *groups) {
+    if (!t) return fail(SPT_EINVAL, "tensor_l2_blocks: NULL tensor");
+    if (mode < 0 || mode >= t->d) return fail(SPT_EINVAL, "tensor_l2_blocks: bad mode");
+    if (blocked_mode) *blocked_mode = t->blk_buf[mode] ? t->blk_mode[mode] : -1;
+    if (block_rows) *block_rows = t->blk_buf[mode] ? t->blk_rows[mode] : 0;
+    if (groups) *groups = t->blk_buf[mode] ? (int64_t)t->blk_off[mode].size() - 1 : 0;
     return SPT_OK;
 }
 

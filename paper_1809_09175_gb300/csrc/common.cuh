@@ -6,6 +6,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "../../include/spt.h"
 
@@ -71,6 +72,16 @@ struct spt_tensor_s {
     // estimate of the rounding error of long fp32 chains of adds)
     double cnt_s2[SPT_MAX_ORDER] = {0.0};
     double cnt_s3[SPT_MAX_ORDER] = {0.0};
+    // per mode, optional: the L2-blocked copy of the mode-sorted records --
+    // grouped by blocks of blk_rows[n] rows of mode blk_mode[n] (each group in
+    // the sorted copy's order, padded to a multiple of 4 records with
+    // zero-valued copies of its last record), record offsets of the groups in
+    // blk_off[n] (groups + 1 entries); the sorted traversal then runs one
+    // launch per group, which gathers only that block of the mode's factor
+    void *blk_buf[SPT_MAX_ORDER] = {nullptr};
+    int blk_mode[SPT_MAX_ORDER] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    int64_t blk_rows[SPT_MAX_ORDER] = {0};
+    std::vector<int64_t> blk_off[SPT_MAX_ORDER];
 };
 
 // ---- host error handling -------------------------------------------------

@@ -663,7 +663,7 @@ spt_status cp_als_step(spt_tensor t, void *const *factors, spt_dtype fdt, int ra
     for (int m = 0; m < t->d; ++m) fp[m] = factors[m];
     uint64_t state = 0;
     for (int m = 0; m < t->d; ++m)
-        state = state * 4 + (t->sorted_buf[m] ? 2 : (t->perm[m] ? 1 : 0));
+        state = state * 4 + (t->blk_buf[m] ? 3 : t->sorted_buf[m] ? 2 : (t->perm[m] ? 1 : 0));
     GraphKey key(t, state, (int)fdt, rank, ld, fp[0], fp[1], fp[2], fp[3], fp[4], lambda, fit_out,
                  workspace, nullptr, t->d);
     if (st != 0) {

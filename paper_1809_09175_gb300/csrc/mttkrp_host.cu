@@ -458,6 +458,25 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
            (int64_t)cps * sm_count() * waves < need)
         waves *= 2;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)cps * sm_count() * waves, need));
+    if (kmode == M_SORTED && !gcp && !det && t->blk_buf[mode]) {
+        // the L2-blocked copy: one launch per group of records (one block of
+        // the blocked mode's rows), each adding the rows it owns
+        const std::vector<int64_t> &off = t->blk_off[mode];
+        const int rw = record_words(t->d);
+        p.accum = 1;
+        for (size_t b = 0; b + 1 < off.size(); ++b) {
+            const int64_t nb = off[b + 1] - off[b];
+            if (nb == 0) continue;
+            p.rec = reinterpret_cast<const int32_t *>(t->blk_buf[mode]) + off[b] * rw;
+            p.nnz = nb;
+            p.nchunks = (nb + npw - 1) / npw;
+            const int64_t nd = (p.nchunks + wpc - 1) / wpc;
+            const int bl = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)cps * sm_count(), nd));
+            fn<<<bl, wpc * 32, smem, st>>>(p);
+            SPT_LAUNCH_CHECK("mttkrp_kernel launch (L2-blocked copy)");
+        }
+        return SPT_OK;
+    }
     if (det) return launch_det(fn, p, blocks, wpc, smem, ab, st);
     if (p.nrep > 1) {
         while (p.nrep > 1 && p.nrep > blocks) p.nrep >>= 1;  // a copy per CTA at most

@@ -93,6 +93,9 @@ struct MttkrpParams {
     const int32_t *hot_rows;  // nhot row ids, hottest first
     int nhot;
     int hot_log2T;            // hash table of 1 << hot_log2T slots (>= 2 nhot)
+    int accum;                // M_SORTED: every row sum is added to the output (vector atomic
+                              // adds), none stored: one launch of several over the groups of
+                              // an L2-blocked copy
     int nrep;                 // M_ATOMIC: copies of the output (a power of two, >= 1); CTA b
     int64_t rep_stride;       // adds into copy b & (nrep - 1), rep_stride elements apart
                               // (out is then a scratch summed into the output afterwards)
@@ -294,6 +297,7 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
             }
             AT *dst = reinterpret_cast<AT *>(p.out) + (int64_t)row * p.old;
             if (MODE == M_ATOMIC) dst += (int64_t)(blockIdx.x & (p.nrep - 1)) * p.rep_stride;
+            if (MODE == M_SORTED && p.accum) atomic = true;  // rows add up across launches
             if (DET && atomic && dslot >= 0) {  // deterministic: this warp's slot
                 const int slot = 2 * (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) + dslot;
                 dst = reinterpret_cast<AT *>(p.det_vals) + (int64_t)slot * p.old;

@@ -446,6 +446,10 @@ spt_status build_perm_mode(spt_tensor t, int n, bool index_only, cudaStream_t st
     // release an earlier build of this mode
     if (t->perm[n]) { cudaFreeAsync(t->perm[n], st); t->perm[n] = nullptr; }
     if (t->sorted_buf[n]) { cudaFreeAsync(t->sorted_buf[n], st); t->sorted_buf[n] = nullptr; }
+    if (t->blk_buf[n]) { cudaFreeAsync(t->blk_buf[n], st); t->blk_buf[n] = nullptr; }  // built from the old copy
+    t->blk_off[n].clear();
+    t->blk_mode[n] = -1;
+    t->blk_rows[n] = 0;
     int32_t *perm = nullptr, *srows = nullptr;
     spt_status s = dmalloc((void **)&perm, seg_bytes(P, 4), st);
     if (!s) s = dmalloc((void **)&srows, seg_bytes(P, 4), st);
@@ -584,6 +588,109 @@ __global__ void hot_compact_kernel(const int32_t *cnt, const int32_t *flag, cons
 // Per mode: count each row's nonzeros, keep the rows with at least
 // SPT_HOT_MIN_COUNT of them (in row order, by a flag scan), sort those by
 // count (stable, so ties stay in row order) and record the first SPT_HOT_MAX.
+// keys[i] = (word k of record i) / block_rows
+__global__ void block_keys_kernel(const int32_t *rec, int rw, int k, int64_t P, int64_t block_rows, uint32_t *keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x)
+        keys[i] = (uint32_t)(rec[i * rw + k] / block_rows);
+}
+
+// record order[i] of src -> dst position i + shift[key[i]] (the stable order
+// by block puts each block's records at its padded offset)
+__global__ void block_scatter_kernel(const int32_t *src, int rw, const int32_t *order, const uint32_t *skeys,
+                                     const int64_t *shift, int64_t P, int32_t *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t *a = src + (int64_t)order[i] * rw;
+        int32_t *b = dst + (i + shift[skeys[i]]) * rw;
+        for (int w = 0; w < rw; ++w) b[w] = a[w];
+    }
+}
+
+// pad slot j of block b: a copy of the block's last record with value 0
+__global__ void block_pad_kernel(const int64_t *pad_at, const int64_t *pad_src, int64_t npad, int rw, int vword,
+                                 int32_t *dst) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < npad; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t *a = dst + pad_src[j] * rw;
+        int32_t *b = dst + pad_at[j] * rw;
+        for (int w = 0; w < rw; ++w) b[w] = w == vword ? 0 : a[w];
+    }
+}
+
+spt_status build_l2_blocks(spt_tensor t, int n, int bm, int64_t block_rows, cudaStream_t st) {
+    const int64_t P = t->nnz;
+    const int d = t->d;
+    const int rw = record_words(d);
+    if (t->blk_buf[n]) { cudaFreeAsync(t->blk_buf[n], st); t->blk_buf[n] = nullptr; }
+    t->blk_off[n].clear();
+    t->blk_mode[n] = -1;
+    t->blk_rows[n] = 0;
+    const int64_t nb = (t->dims[bm] + block_rows - 1) / block_rows;
+    const int k = 1 + (bm < n ? bm : bm - 1);  // the record word of mode bm
+    const int32_t *src = reinterpret_cast<const int32_t *>(t->sorted_buf[n]);
+    uint32_t *keys = nullptr, *skeys = nullptr;
+    int32_t *order = nullptr, *cnt = nullptr;
+    int64_t *dshift = nullptr, *dpad = nullptr;
+    void *buf = nullptr;
+    auto cleanup = [&]() {
+        dfree(keys, st); dfree(skeys, st); dfree(order, st); dfree(cnt, st); dfree(dshift, st); dfree(dpad, st);
+    };
+    spt_status s = dmalloc((void **)&keys, seg_bytes(P, 4), st);
+    if (!s) s = dmalloc((void **)&skeys, seg_bytes(P, 4), st);
+    if (!s) s = dmalloc((void **)&order, seg_bytes(P, 4), st);
+    if (!s) s = dmalloc((void **)&cnt, 4 * nb, st);
+    if (s) { cleanup(); return s; }
+    SPT_CUDA(cudaMemsetAsync(cnt, 0, 4 * nb, st));
+    std::vector<int32_t> hcnt(nb, 0);
+    if (P > 0) {
+        block_keys_kernel<<<grid_for(P, 256), 256, 0, st>>>(src, rw, k, P, block_rows, keys);
+        s = radix_sort_pairs(keys, nullptr, P, bit_width_u32((uint64_t)(nb - 1)), skeys, order, st);
+        if (s) { cleanup(); return s; }
+        slice_count_kernel<<<grid_for(P, 256), 256, 0, st>>>(reinterpret_cast<const int32_t *>(skeys), P, cnt);
+        SPT_LAUNCH_CHECK("block key kernels");
+        cudaError_t e = cudaMemcpyAsync(hcnt.data(), cnt, 4 * nb, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "build_l2_blocks counts"); }
+    }
+    // padded offsets (multiples of 4 records keep every group 16-byte aligned)
+    std::vector<int64_t> off(nb + 1, 0), shift(nb, 0), pad_at, pad_src;
+    int64_t start = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        const int64_t c = hcnt[b], pc = (c + 3) & ~int64_t(3);
+        off[b + 1] = off[b] + pc;
+        shift[b] = off[b] - start;
+        for (int64_t j = c; j < pc; ++j) {
+            pad_at.push_back(off[b] + j);
+            pad_src.push_back(off[b] + c - 1);
+        }
+        start += c;
+    }
+    const int64_t npad = (int64_t)pad_at.size();
+    s = dmalloc(&buf, seg_bytes(std::max<int64_t>(1, off[nb]) * rw, 4), st);
+    if (!s) s = dmalloc((void **)&dshift, sizeof(int64_t) * std::max<int64_t>(1, nb), st);
+    if (!s) s = dmalloc((void **)&dpad, sizeof(int64_t) * std::max<int64_t>(1, 2 * npad), st);
+    if (s) { cleanup(); dfree(buf, st); return s; }
+    std::vector<int64_t> hpad(pad_at);
+    hpad.insert(hpad.end(), pad_src.begin(), pad_src.end());
+    cudaError_t e = cudaMemcpyAsync(dshift, shift.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && npad > 0)
+        e = cudaMemcpyAsync(dpad, hpad.data(), sizeof(int64_t) * 2 * npad, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { cleanup(); dfree(buf, st); return cuda_fail(e, "build_l2_blocks tables"); }
+    if (P > 0)
+        block_scatter_kernel<<<grid_for(P, 256), 256, 0, st>>>(src, rw, order, skeys, dshift, P,
+                                                               reinterpret_cast<int32_t *>(buf));
+    if (npad > 0)
+        block_pad_kernel<<<grid_for(npad, 256), 256, 0, st>>>(dpad, dpad + npad, npad, rw, d,
+                                                              reinterpret_cast<int32_t *>(buf));
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host tables go out of scope
+    cleanup();
+    if (e != cudaSuccess) { dfree(buf, st); return cuda_fail(e, "build_l2_blocks copy"); }
+    t->blk_buf[n] = buf;
+    t->blk_off[n] = off;
+    t->blk_mode[n] = bm;
+    t->blk_rows[n] = block_rows;
+    return SPT_OK;
+}
+
 spt_status build_hot_rows(spt_tensor t, cudaStream_t st) {
     const int64_t P = t->nnz;
     if (!t->hot_buf) {

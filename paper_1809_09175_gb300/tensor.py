@@ -84,6 +84,14 @@ class SparseTensor:
         flags = (B.SPT_PERM_INDEX_ONLY if index_only else 0) | (B.SPT_PERM_SLICE_ORDER if slice_order else 0)
         B.build_mode_permutation(self.handle, mode, flags, _stream())
 
+    def build_l2_blocks(self, mode: int, blocked_mode: int = -1, block_rows: int = -1):
+        """The mode's L2-blocked copy (build_mode_l2_blocks); block_rows = 0 drops it."""
+        B.build_mode_l2_blocks(self.handle, mode, blocked_mode, block_rows, _stream())
+
+    def l2_blocks(self, mode: int):
+        """(blocked mode or -1, rows per block, groups) of the mode's L2-blocked copy."""
+        return B.tensor_l2_blocks(self.handle, mode)
+
     def permutation(self, mode: int) -> torch.Tensor:
         out = torch.empty(self.nnz, dtype=torch.int32, device="cuda")
         B.tensor_get_permutation(self.handle, mode, out.data_ptr(), _stream())

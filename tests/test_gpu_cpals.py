@@ -60,8 +60,11 @@ def _gram_hadamard_conds(A_old, A_new):
     return conds
 
 
-def _one_step(P, idx, vals, dims, R, facs_np):
+def _one_step(P, idx, vals, dims, R, facs_np, block_rows=None):
     T, facs, lam, fit, ws = _setup(P, idx, vals, dims, R, facs_np)
+    if block_rows is not None:  # every mode's sorted traversal over its L2-blocked copy
+        for m in range(len(dims)):
+            T.build_l2_blocks(m, -1, block_rows)
     A = [f[:, :R].astype(np.float64).copy() for f in facs_np]
     A_old = [a.copy() for a in A]
     T.cp_als_step(facs, R, lam, fit, ws)
@@ -95,6 +98,17 @@ def test_one_step_matches_oracle_power_law(dims, nnz, s, R, seed):
     P = _lib()
     idx, vals = synth.coo_zipf(dims, nnz, s, seed)
     _one_step(P, idx, vals, dims, R, synth.factor_matrices(dims, R, seed, "uniform"))
+
+
+def test_one_step_over_l2_blocked_copies():
+    """CP-ALS whose MTTKRPs run over L2-blocked copies (blocks of 37 rows of
+    the longest other mode: one launch per block, rows added across
+    launches) meets the same one-step gates against the oracle."""
+    P = _lib()
+    dims = (600, 500, 400)
+    idx, vals = synth.coo_zipf(dims, 120_000, 1.0, 21)
+    facs_np = synth.factor_matrices(dims, 16, 21, "uniform")
+    _one_step(P, idx, vals, dims, 16, facs_np, block_rows=37)
 
 
 def test_ten_iterations_fit_trajectory():

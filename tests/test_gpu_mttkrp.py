@@ -421,3 +421,49 @@ def test_atomic_scatter_on_a_short_mode_with_long_rows(R):
     T.close()
     ref = oracle.mttkrp_threads(idx, vals, dims, [widen(f, "f32", R) for f in facs], 0, R, os.cpu_count() or 4)
     assert rel_fro(got, ref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("order", [3, 4])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_l2_blocked_copy(order, dtype):
+    """The sorted traversal over an L2-blocked copy (one launch per block of
+    the longest other mode's rows, each adding the rows it owns): every mode
+    against the oracle for blocks of 1 row (many empty groups), 97 rows
+    (ragged groups with padding records) and 1000 rows, two chunk shapes;
+    dropping the copy restores the plain traversal; the deterministic call
+    keeps the plain copy; bad arguments are refused."""
+    P = _lib()
+    dims = {3: (3000, 200, 150), 4: (2500, 120, 60, 30)}[order]
+    R = 20
+    idx, vals = synth.coo_zipf(dims, 150_000, 1.0, 80 + order)
+    facs = synth.factor_matrices(dims, R, 80 + order, "normal", dtype=dtype)
+    T = P.SparseTensor(idx, vals, dims)
+    T.build_permutation(slice_order=True)
+    dev = [to_device_factor(f, dtype) for f in facs]
+    for n in range(order):
+        ref = _oracle(idx, vals, dims, facs, dtype, R, n)
+        bm = max((m for m in range(order) if m != n), key=lambda m: dims[m])
+        for rows in (1, 97, 1000):
+            T.build_l2_blocks(n, -1, rows)
+            assert T.l2_blocks(n) == (bm, rows, -(-dims[bm] // rows))
+            for S_, lanes, warps in [(7, 8, 4), (23, 4, 8)]:
+                sc = P.spt_schedule.make("sorted", lanes_per_nnz=lanes, chunks=1 if lanes * 4 >= R else 2,
+                                         nnz_per_group=S_, warps_per_cta=warps)
+                got = T.mttkrp(n, dev, R, sched=sc).cpu().numpy()
+                assert rel_fro(got[:, :R], ref) <= TOL[dtype], (n, rows, S_, lanes)
+                assert np.all(got[:, R:] == 0)
+        det = T.mttkrp(n, dev, R, deterministic=True).cpu().numpy()[:, :R]
+        assert rel_fro(det, ref) <= TOL[dtype]
+        T.build_l2_blocks(n, block_rows=0)
+        assert T.l2_blocks(n)[0] == -1
+        assert rel_fro(T.mttkrp(n, dev, R).cpu().numpy()[:, :R], ref) <= TOL[dtype]
+    with pytest.raises(P.SptError):
+        T.build_l2_blocks(0, 0, 10)  # the blocked mode is the mode itself
+    T.check()
+    T.close()
+    T2 = P.SparseTensor(idx, vals, dims)
+    T2.build_permutation(index_only=True)
+    with pytest.raises(P.SptError) as e:
+        T2.build_l2_blocks(0)  # no mode-sorted copy
+    assert e.value.status == P.SPT_ESTATE
+    T2.close()
