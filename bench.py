@@ -538,7 +538,8 @@ def run_ours(args):
 def full_parity(args, P, torch, w, T, idx, vals, R, d, outs, sched_for):
     """Relative Frobenius error of the whole output of every mode against the
     FP64 oracle (its all-core form, outside any timed region): the sorted,
-    perm_n, atomic and private scatters and the deterministic call, with fp32
+    perm_n (over the coordinate arrays, and over the storage-order records),
+    atomic and private scatters and the deterministic call, with fp32
     and with bf16 factors.  The gate compares with the oracle fed the same
     stored factor values (1e-5 for fp32, 2e-3 for bf16); for bf16 the error
     against the un-rounded fp32 factors (the quantisation included) is
@@ -558,17 +559,22 @@ def full_parity(args, P, torch, w, T, idx, vals, R, d, outs, sched_for):
         for n in range(d):
             ref = oracle.mttkrp_threads(idx, vals, w.dims, A64, n, R, th)
             den = np.linalg.norm(ref)
-            for sc in ["sorted", "perm", "atomic", "private", "deterministic"]:
+            for sc in ["sorted", "perm", "perm_rec", "atomic", "private", "deterministic"]:
                 if sc in ("sorted", "perm", "deterministic") and args.scatter == "perm" and sc != "perm":
                     continue
                 try:
-                    s = sched_for(n, "sorted" if sc == "deterministic" else sc, fdt)
+                    if sc == "perm_rec":  # perm_n over the storage-order records
+                        T.storage_records(True)
+                    s = sched_for(n, {"deterministic": "sorted", "perm_rec": "perm"}.get(sc, sc), fdt)
                     if sc == "deterministic" and s.lanes_per_nnz * s.chunks * 4 < R:
                         s = None
                     T.mttkrp(n, fd, R, out=outs[n], sched=s, deterministic=(sc == "deterministic"))
                 except P.SptError:  # private: this mode's output copy does not fit a cluster
                     errs.setdefault(sc, []).append(None)
                     continue
+                finally:
+                    if sc == "perm_rec":
+                        T.storage_records(False)
                 got = outs[n][:, :R].double().cpu().numpy()
                 errs.setdefault(sc, []).append(float(np.linalg.norm(got - ref) / den))
                 if fdt == "bf16" and sc == "sorted":
@@ -600,10 +606,11 @@ def measure_extras(args, P, torch, w, T, idx, vals, facs_np, dtype, R, d, ld, ou
     for fdt in ["f32", "bf16"]:
         fnp = w.factors(R, fdt)
         fd = [_dev_factor(torch, f, fdt) for f in fnp]
-        for sc in (["sorted"] if args.scatter != "perm" else []) + ["perm", "atomic", "private"]:
+        for sc in (["sorted"] if args.scatter != "perm" else []) + ["perm", "perm_rec", "atomic", "private"]:
             ms = []
+            T.storage_records(sc == "perm_rec")  # perm_rec: perm_n over the storage-order records
             for n in range(d):
-                s = sched_for(n, sc, fdt)
+                s = sched_for(n, "perm" if sc == "perm_rec" else sc, fdt)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 try:
@@ -632,6 +639,7 @@ def measure_extras(args, P, torch, w, T, idx, vals, facs_np, dtype, R, d, ld, ou
                     got = outs[n][torch.from_numpy(rows).long().cuda(), :R].double().cpu().numpy()
                     ref = oracle.mttkrp_rows(idx, vals, w.dims, A64, n, R, rows)
                     errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+            T.storage_records(False)
             ran = [m for m in ms if m is not None]
             var[f"{sc}/{fdt}"] = {"ms_per_mode": ms,
                                   "nnzR_per_s": w.nnz * R * len(ran) / (sum(ran) / 1e3) if ran else None,

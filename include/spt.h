@@ -156,6 +156,16 @@ spt_status tensor_check(spt_tensor t, void *stream);
  * radix sort borrows 16P bytes of temporary device memory. */
 spt_status build_mode_permutation(spt_tensor t, int mode, int flags, void *stream);
 
+/* keep = 1: pack the nonzeros, in storage order, into records of their d
+ * coordinates and the value's bits (4 words each for d <= 3, 6 for d = 4, 5;
+ * one array shared by every mode), so that the perm_n traversal
+ * (SPT_SCATTER_PERM, the paper's Fig. MTTKRP-C) reads one record per nonzero
+ * through perm_n instead of d + 1 separate scattered words; keep = 0 drops
+ * them (the traversal then reads the coordinate arrays again).  Memory: 16P
+ * or 24P bytes.  Stream-ordered.  Errors: SPT_EINVAL for a NULL tensor or a
+ * keep other than 0 or 1. */
+spt_status tensor_storage_records(spt_tensor t, int keep, void *stream);
+
 /* Rows per block of build_mode_l2_blocks when block_rows < 0: 48 MB of
  * factor rows at 256 bytes a row (R = 64 in fp32), about a third of L2. */
 #define SPT_L2_BLOCK_ROWS_DEFAULT 196608

@@ -159,6 +159,7 @@ _try_sig("mttkrp_batch_destroy", _vp)
 _try_sig("spt_set_wait_tries", C.c_int64)
 _try_sig("spt_row_gather_probe", C.c_int, _vp, C.c_int64, _vp, C.c_int64, _vp, _vp, C.c_int64, _vp, _vp, _vp)
 _try_sig("tensor_create_shard", _vp, C.c_int, C.c_int64, C.c_int64, _vp, C.POINTER(_vp))
+_try_sig("tensor_storage_records", _vp, C.c_int, _vp)
 _try_sig("build_mode_l2_blocks", _vp, C.c_int, C.c_int, C.c_int64, _vp)
 _try_sig("tensor_l2_blocks", _vp, C.c_int, C.POINTER(C.c_int), _i64p, _i64p)
 _try_sig("cp_als_hinv", _vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp)
@@ -322,6 +323,10 @@ def cp_als_step(t: int, factor_ptrs: Sequence[int], fdt, rank: int, ld: int, lam
 
 def cp_als_status(workspace_ptr: int, stream: int = 0):
     _chk(_L.cp_als_status(workspace_ptr, stream or None))
+
+
+def tensor_storage_records(t: int, keep: int = 1, stream: int = 0):
+    _chk(_L.tensor_storage_records(t, int(keep), stream or None))
 
 
 SPT_L2_BLOCK_ROWS_DEFAULT = 196608

@@ -78,6 +78,7 @@ spt_status free_tensor_buffers(spt_tensor t) {
     dfree(t->coo_buf, st);
     dfree(t->dev_err, st);
     dfree(t->hot_buf, st);
+    dfree(t->srec, st);
     cudaError_t e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? SPT_OK : cuda_fail(e, "tensor_destroy");
 }
@@ -276,6 +277,19 @@ spt_status build_mode_permutation(spt_tensor t, int mode, int flags, void *strea
         if (s) return s;
     }
     return SPT_OK;
+}
+
+spt_status tensor_storage_records(spt_tensor t, int keep, void *stream) {
+    if (!t) return fail(SPT_EINVAL, "tensor_storage_records: NULL tensor");
+    if (keep != 0 && keep != 1) return fail(SPT_EINVAL, "tensor_storage_records: keep must be 0 or 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    drop_graphs(t);
+    if (!keep) {
+        dfree(t->srec, st);
+        t->srec = nullptr;
+        return SPT_OK;
+    }
+    return t->srec ? SPT_OK : build_storage_records(t, st);
 }
 
 spt_status build_mode_l2_blocks(spt_tensor t, int mode, int blocked_mode, int64_t block_rows, void *stream) {

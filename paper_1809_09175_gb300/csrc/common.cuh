@@ -78,6 +78,10 @@ struct spt_tensor_s {
     // zero-valued copies of its last record), record offsets of the groups in
     // blk_off[n] (groups + 1 entries); the sorted traversal then runs one
     // launch per group, which gathers only that block of the mode's factor
+    // optional: every nonzero in storage order as one record (its d
+    // coordinates, the value's bits, zero padding to record_words(d) words),
+    // read through perm_n by the perm_n traversal
+    int32_t *srec = nullptr;
     void *blk_buf[SPT_MAX_ORDER] = {nullptr};
     int blk_mode[SPT_MAX_ORDER] = {-1, -1, -1, -1, -1, -1, -1, -1};
     int64_t blk_rows[SPT_MAX_ORDER] = {0};

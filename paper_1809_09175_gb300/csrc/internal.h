@@ -15,6 +15,8 @@ spt_status radix_sort_pairs(const uint32_t *keys_in, const int32_t *vals_in, int
                             uint32_t *keys_out, int32_t *vals_out, cudaStream_t st);
 spt_status coalesce_tensor(spt_tensor t, cudaStream_t st);
 spt_status build_perm_mode(spt_tensor t, int n, bool index_only, cudaStream_t st, bool slice_order = false);
+// t->srec: every nonzero in storage order as one packed record.
+spt_status build_storage_records(spt_tensor t, cudaStream_t st);
 // The L2-blocked copy of mode n's sorted records (t->blk_*[n]), blocks of
 // block_rows rows of mode bm; needs the mode-sorted copy; synchronises `st`.
 spt_status build_l2_blocks(spt_tensor t, int n, int bm, int64_t block_rows, cudaStream_t st);

@@ -302,7 +302,8 @@ spt_status launch_mttkrp(spt_tensor t, int mode, const void *const *factors, spt
     p.rows = t->idx[mode];
     p.vals = t->vals;
     p.perm = t->perm[mode];
-    p.rec = reinterpret_cast<const int32_t *>(t->sorted_buf[mode]);
+    p.rec = kmode == M_PERM ? t->srec : reinterpret_cast<const int32_t *>(t->sorted_buf[mode]);
+    p.mode = mode;
     int q = 0;
     for (int m = 0; m < t->d; ++m) {
         if (m == mode) continue;

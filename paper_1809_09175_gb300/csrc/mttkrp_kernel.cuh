@@ -72,7 +72,8 @@ struct MttkrpParams {
     const int32_t *oidx[4];  // M_ATOMIC / M_PERM: coordinates of the other modes
     const float *vals;       // M_ATOMIC / M_PERM: values
     const int32_t *perm;     // M_PERM: traversal position -> storage position
-    const int32_t *rec;      // M_SORTED: packed records in mode-n order
+    const int32_t *rec;      // M_SORTED: packed records in mode-n order; M_PERM, nullable: the
+                             // storage-order records (all d coordinates, then the value)
     const void *fac[4];      // factor matrices of the other modes
     int fld;                 // factor row stride (elements)
     const void *lambda;      // nullable; accumulator type (float, double for fp64)
@@ -115,6 +116,7 @@ struct MttkrpParams {
     const void *fac_n;   // the mode's own factor A^(n): the model value needs it
     int loss;            // 0 Poisson (stored part), 1 Bernoulli-logit, 2 Gaussian
     double *loss_out;    // nullable: sum of the stored entries' loss terms
+    int mode;            // n (M_PERM over storage-order records: the output row's word)
 };
 
 __device__ __forceinline__ uint4 ldg16(const void *p) {
@@ -343,10 +345,34 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
                 x = __int_as_float(w[D1 + 1]);
             } else if (MODE == M_PERM) {
                 const int q = buf[e];
-                row = __ldg(p.rows + q);
-                x = __ldg(p.vals + q);
+                if (p.rec) {  // one storage-order record per nonzero: its coordinates, then the value
+                    int w[REC];
+                    const int32_t *rp = p.rec + (int64_t)q * REC;
+                    if (REC == 4) {
+                        const int4 v = __ldg(reinterpret_cast<const int4 *>(rp));
+                        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+                    } else {
 #pragma unroll
-                for (int m = 0; m < D1; ++m) r[m] = __ldg(p.oidx[m] + q);
+                        for (int h = 0; h < REC; h += 2) {
+                            const int2 v = __ldg(reinterpret_cast<const int2 *>(rp + h));
+                            w[h] = v.x;
+                            w[h + 1] = v.y;
+                        }
+                    }
+                    // word n is the row; the others in increasing mode order
+                    row = w[0];
+#pragma unroll
+                    for (int m = 1; m <= D1; ++m)
+                        if (m == p.mode) row = w[m];
+#pragma unroll
+                    for (int m = 0; m < D1; ++m) r[m] = m < p.mode ? w[m] : w[m + 1];
+                    x = __int_as_float(w[D1 + 1]);
+                } else {
+                    row = __ldg(p.rows + q);
+                    x = __ldg(p.vals + q);
+#pragma unroll
+                    for (int m = 0; m < D1; ++m) r[m] = __ldg(p.oidx[m] + q);
+                }
             } else {
                 row = buf[e];
                 x = __int_as_float(buf[(D1 + 1) * npw + e]);

@@ -588,6 +588,31 @@ __global__ void hot_compact_kernel(const int32_t *cnt, const int32_t *flag, cons
 // Per mode: count each row's nonzeros, keep the rows with at least
 // SPT_HOT_MIN_COUNT of them (in row order, by a flag scan), sort those by
 // count (stable, so ties stay in row order) and record the first SPT_HOT_MAX.
+// rec[i] = {idx[0][i], ..., idx[d-1][i], bits(vals[i]), 0 pad}
+__global__ void storage_records_kernel(IdxPtrs idx, int d, const float *vals, int64_t P, int rw, int32_t *rec) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t *r = rec + i * rw;
+        for (int m = 0; m < d; ++m) r[m] = idx.p[m][i];
+        r[d] = __float_as_int(vals[i]);
+        for (int k = d + 1; k < rw; ++k) r[k] = 0;
+    }
+}
+
+spt_status build_storage_records(spt_tensor t, cudaStream_t st) {
+    const int rw = record_words(t->d);
+    int32_t *rec = nullptr;
+    spt_status s = dmalloc((void **)&rec, seg_bytes(std::max<int64_t>(1, t->nnz) * rw, 4), st);
+    if (s) return s;
+    IdxPtrs ip;
+    for (int m = 0; m < t->d; ++m) ip.p[m] = t->idx[m];
+    if (t->nnz > 0)
+        storage_records_kernel<<<grid_for(t->nnz, 256), 256, 0, st>>>(ip, t->d, t->vals, t->nnz, rw, rec);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { dfree(rec, st); return cuda_fail(e, "build_storage_records"); }
+    t->srec = rec;
+    return SPT_OK;
+}
+
 // keys[i] = (word k of record i) / block_rows
 __global__ void block_keys_kernel(const int32_t *rec, int rw, int k, int64_t P, int64_t block_rows, uint32_t *keys) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x)

@@ -84,6 +84,10 @@ class SparseTensor:
         flags = (B.SPT_PERM_INDEX_ONLY if index_only else 0) | (B.SPT_PERM_SLICE_ORDER if slice_order else 0)
         B.build_mode_permutation(self.handle, mode, flags, _stream())
 
+    def storage_records(self, keep: bool = True):
+        """Pack (or drop) the storage-order records the perm_n traversal reads."""
+        B.tensor_storage_records(self.handle, keep, _stream())
+
     def build_l2_blocks(self, mode: int, blocked_mode: int = -1, block_rows: int = -1):
         """The mode's L2-blocked copy (build_mode_l2_blocks); block_rows = 0 drops it."""
         B.build_mode_l2_blocks(self.handle, mode, blocked_mode, block_rows, _stream())

@@ -467,3 +467,37 @@ def test_l2_blocked_copy(order, dtype):
         T2.build_l2_blocks(0)  # no mode-sorted copy
     assert e.value.status == P.SPT_ESTATE
     T2.close()
+
+
+@pytest.mark.parametrize("order", [2, 3, 4, 5])
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f64"])
+def test_perm_traversal_over_storage_records(order, dtype):
+    """The perm_n traversal (Fig. MTTKRP-C) reading one storage-order record
+    per nonzero (`tensor_storage_records`: 4-word records for orders 2-3,
+    6-word ones for 4-5) against the oracle on every mode, two chunk shapes,
+    and against the same traversal over the separate coordinate arrays (the
+    same tensor once the records are dropped)."""
+    P = _lib()
+    dims = {2: (700, 500), 3: (400, 300, 200), 4: (300, 200, 100, 50), 5: (200, 150, 100, 50, 20)}[order]
+    R = 20
+    idx, vals = synth.coo_zipf(dims, 60_000, 1.1, 90 + order)
+    facs = synth.factor_matrices(dims, R, 90 + order, "normal", dtype=dtype)
+    dev = [to_device_factor(f, dtype) for f in facs]
+    T = P.SparseTensor(idx, vals, dims)
+    T.build_permutation(index_only=True)
+    scheds = [P.spt_schedule.make("perm", lanes_per_nnz=lanes, chunks=1 if lanes * 4 >= R else 2,
+                                  nnz_per_group=S_, warps_per_cta=4) for S_, lanes in [(7, 8), (23, 4)]]
+    T.storage_records()
+    T.storage_records()  # a second call keeps the records
+    got = [[T.mttkrp(n, dev, R, sched=sc).cpu().numpy() for sc in scheds] for n in range(order)]
+    T.storage_records(False)
+    plain = [[T.mttkrp(n, dev, R, sched=sc).cpu().numpy() for sc in scheds] for n in range(order)]
+    for n in range(order):
+        ref = _oracle(idx, vals, dims, facs, dtype, R, n)
+        for k in range(len(scheds)):
+            assert rel_fro(got[n][k][:, :R], ref) <= TOL[dtype], (n, k)
+            assert rel_fro(got[n][k][:, :R], plain[n][k][:, :R]) <= TOL[dtype]
+    with pytest.raises(P.SptError):
+        P.tensor_storage_records(T.handle, 2)
+    T.check()
+    T.close()

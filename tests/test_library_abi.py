@@ -55,6 +55,7 @@ def test_argument_errors_without_device():
     assert L.mttkrp_deterministic(None, 0, None, 0, 8, 8, None, None, None, None) == P.SPT_EINVAL
     assert L.gcp_gradient(None, 0, None, 0, 8, 8, 0, None, None, None) == P.SPT_EINVAL
     assert L.build_mode_l2_blocks(None, 0, -1, -1, None) == P.SPT_EINVAL
+    assert L.tensor_storage_records(None, 1, None) == P.SPT_EINVAL
     assert L.tensor_l2_blocks(None, 0, None, None, None) == P.SPT_EINVAL
     for bad in (-2, 1 << 32):  # the wait budget is host state: checked without a device
         with pytest.raises(P.SptError) as ei:
