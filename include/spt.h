@@ -505,7 +505,9 @@ spt_status cp_als_workspace_size(spt_tensor t, int rank, int ld, size_t *bytes);
 
 /* One CP-ALS iteration over all modes n = 0..d-1 in order (Sec. 3, ALS):
  *   V = MTTKRP_n(X, A) (unit weights); H = elementwise product over m != n of
- *   A^(m)T A^(m) (FP64); Cholesky H = L L^T (FP64, one retry with a ridge of
+ *   A^(m)T A^(m) (FP64); H^-1 in FP64 by symmetric elimination, whose pivots
+ *   are the squared diagonal of the Cholesky factor H = L L^T (so it succeeds
+ *   exactly when H is positive definite; one retry with a ridge of
  *   1e-12 trace(H)/R); A^(n) = V H^-1; lambda_j = ||A^(n)(:,j)||_2 (FP64) and
  *   A^(n)(:,j) /= lambda_j; 16-bit factors are rounded (nearest even) after
  *   normalising.  After the last mode, fit = 1 - ||X - M|| / ||X|| with
@@ -533,10 +535,12 @@ spt_status cp_als_step(spt_tensor t, void *const *factors, spt_dtype fdt, int ra
  * the last mode, cp_als_fit.  Stream-ordered, no synchronisation.
  *
  * cp_als_hinv: H = elementwise product over m != mode of the R x R FP64
- *   Grams G (device, order * R * R doubles, G_m at G + m R R); Cholesky
- *   H = L L^T in FP64 with one retry at a ridge of 1e-12 trace(H)/R; hinv
- *   (device, R * R float32) = H^-1.  If H is not positive definite after the
- *   ridge, *status (device int) is set to 2 and hinv to the identity. */
+ *   Grams G (device, order * R * R doubles, G_m at G + m R R); hinv (device,
+ *   R * R float32) = H^-1 by Gauss-Jordan elimination in FP64 without
+ *   pivoting, whose pivots are the squared diagonal of the Cholesky factor
+ *   H = L L^T, with one retry at a ridge of 1e-12 trace(H)/R.  If a pivot is
+ *   <= 0 after the ridge (H not positive definite), *status (device int) is
+ *   set to 2 and hinv to the identity. */
 spt_status cp_als_hinv(const double *G, int order, int mode, int rank, float *hinv, int *status, void *stream);
 
 /* cp_als_apply: A32 = V hinv for `rows` rows of V (device, rows x ld float32,

@@ -3,8 +3,9 @@
 //
 // Per mode n (in order 0..d-1):
 //   1. V = MTTKRP_n(X, A)                                (mttkrp kernel)
-//   2. H = *_{m != n} G_m, Cholesky H = L L^T, W = L^-1,
-//      Hinv = W^T W                                       (one CTA, FP64)
+//   2. H = *_{m != n} G_m, Hinv = H^-1 by symmetric Gauss-Jordan
+//      elimination, whose pivots are the squared diagonal of H's
+//      Cholesky factor                                    (one CTA, FP64)
 //   3. A32 = V Hinv, colsq_j = sum_k A32(k,j)^2           (FP32 FMAs, FP64 sums)
 //   4. lambda_j = sqrt(colsq_j), A^(n) = A32 / lambda   -> stored type
 //      (round to nearest even for 16-bit factors)
@@ -90,9 +91,13 @@ __host__ __device__ inline GramShape gram_shape(int R, int es) {
     while (rpt > 1 && (size_t)2 * RS * rpt * g.stride * es > 48 * 1024) --rpt;
     g.rows_per_team = rpt;
     g.tile_rows = RS * rpt;
-    g.smem = (size_t)2 * g.tile_rows * g.stride * es + sizeof(double) * (size_t)RP * RP;
+    g.smem = (size_t)2 * g.tile_rows * g.stride * es + sizeof(double) * (size_t)RS * RP * RP;
     return g;
 }
+
+// At most this many CTAs per SM run a Gram launch (and so the two-stage
+// reduction holds at most SMs times this many partial Grams).
+inline int gram_ctas_per_sm(int R) { return std::max(1, 1024 / gram_shape(R, 4).threads); }
 
 // G += A^T A over all I rows (A row-major, stride ld, first R columns).
 // Thread (ti, tj) of a team owns the 4 x 4 block G[4ti.., 4tj..] in
@@ -100,10 +105,14 @@ __host__ __device__ inline GramShape gram_shape(int R, int es) {
 // raw stored rows are double buffered with cp.async, so the next tile loads
 // while this one is multiplied.  Entries of G outside R x R (from padding
 // columns, whatever they hold) are dropped at the end.  FP32 partial sums
-// over at most 256 rows are folded into the CTA's FP64 copy of G in shared
-// memory, which each CTA adds to G atomically.
+// over at most 256 rows are folded into the team's FP64 copy of G in shared
+// memory (one writer per entry); at the end the CTA sums its teams' copies
+// in team order and either stores the sum as its R x R block of `partials`
+// (row blockIdx.x; gram_reduce_kernel adds the blocks to G in block order)
+// or, with partials = NULL, adds it to G atomically.
 template <typename FT>
-__global__ void __launch_bounds__(1024) gram_kernel(const FT *A, int64_t I, int ld, int R, double *G) {
+__global__ void __launch_bounds__(1024) gram_kernel(const FT *A, int64_t I, int ld, int R, double *G,
+                                                    double *partials) {
     extern __shared__ __align__(16) unsigned char gsm[];
     const GramShape sh = gram_shape(R, (int)sizeof(FT));
     const int RT = (R + 3) / 4, RP = RT * 4;
@@ -118,22 +127,21 @@ __global__ void __launch_bounds__(1024) gram_kernel(const FT *A, int64_t I, int 
     const int team = threadIdx.x / team_sz, tid = threadIdx.x % team_sz;
     const int ti = tid / RT, tj = tid % RT;
     const int RR = RP * RP;
-    for (int e = threadIdx.x; e < RR; e += blockDim.x) red[e] = 0.0;
+    for (int e = threadIdx.x; e < RS * RR; e += blockDim.x) red[e] = 0.0;
     float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    // fold the FP32 partials into the CTA's FP64 block (each team: its entries)
+    // fold the FP32 partials into the team's FP64 block (a thread: its entries)
     auto fold = [&]() {
         if (team < RS) {
+            double *tred = red + (size_t)team * RR;
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    double *dst = &red[(4 * ti + i) * RP + 4 * tj + j];
-                    if (RS == 1) *dst += (double)acc[i][j];
-                    else atomicAdd(dst, (double)acc[i][j]);
+                    tred[(4 * ti + i) * RP + 4 * tj + j] += (double)acc[i][j];
                     acc[i][j] = 0.f;
                 }
         }
@@ -181,99 +189,139 @@ __global__ void __launch_bounds__(1024) gram_kernel(const FT *A, int64_t I, int 
     __syncthreads();
     for (int e = threadIdx.x; e < RR; e += blockDim.x) {
         const int i = e / RP, j = e % RP;
-        if (i < R && j < R) atomicAdd(G + i * R + j, red[e]);
+        if (i >= R || j >= R) continue;
+        double sum = 0.0;
+        for (int t = 0; t < RS; ++t) sum += red[(size_t)t * RR + e];
+        if (partials) partials[(int64_t)blockIdx.x * R * R + i * R + j] = sum;
+        else atomicAdd(G + i * R + j, sum);
     }
 }
 
-// H = *_{m != n} G_m; Cholesky (one retry with ridge 1e-12 trace/R);
-// Hinv = L^-T L^-1 -> float.  zero_gram / zero_colsq (nullable): R*R and R
-// doubles cleared afterwards for this mode's update (G_n and the column sums).
-// Shared memory: R*R doubles (L in the lower triangle, W = L^-1 strictly
-// below the diagonal stored transposed in the upper triangle) + R doubles.
-__global__ void __launch_bounds__(512) chol_inv_kernel(const double *G, int d, int n, int R, float *Hinv,
-                                                       double *zero_gram, double *zero_colsq, int *status) {
+// G += the sum of the nb partial Grams (R x R each, consecutive): a warp
+// per entry, lane l adding blocks l, l + 32, ... (four loads in flight), the
+// lanes' sums combined by a fixed shuffle tree, so the order of additions is
+// fixed by nb alone.
+__global__ void __launch_bounds__(256) gram_reduce_kernel(const double *partials, int nb, int RR, double *G) {
+    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= RR) return;  // warp-uniform
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int b = lane;
+    for (; b + 96 < nb; b += 128) {
+        s0 += partials[(int64_t)b * RR + e];
+        s1 += partials[(int64_t)(b + 32) * RR + e];
+        s2 += partials[(int64_t)(b + 64) * RR + e];
+        s3 += partials[(int64_t)(b + 96) * RR + e];
+    }
+    for (; b < nb; b += 32) s0 += partials[(int64_t)b * RR + e];
+    double sum = (s0 + s1) + (s2 + s3);
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) G[e] += sum;
+}
+
+// H = *_{m != n} G_m and Hinv = H^-1 -> float, in FP64 with the sweep
+// operator (Gauss-Jordan elimination kept symmetric; Goodnight, "A tutorial
+// on the SWEEP operator", 1979): sweeping pivot k of a symmetric M with
+// d = M(k,k) sets M(i,j) -= M(i,k) M(k,j) / d for i, j != k, M(i,k) =
+// M(k,i) = M(i,k) / d, and M(k,k) = -1 / d; after every pivot M = -H^-1.
+// Pivot k is the k-th diagonal entry of the Schur complement left by the
+// earlier pivots -- the square L_kk^2 of H's Cholesky factor H = L L^T -- so
+// the sweep runs to the end exactly when the Cholesky factorisation exists;
+// a pivot <= 0 means H is not positive definite: one retry with a ridge of
+// 1e-12 trace(H)/R, then the singular status and Hinv = identity.  M stays
+// symmetric, so each step updates the R(R+1)/2 pairs i <= j with one FP64
+// FMA each (GB300's FP64 rate is ~1/70 of its FP32 rate, so the FP64 work
+// sets the time at larger R), all pairs at once: the critical path is 2R
+// barriers, and the reciprocal of the next pivot is taken by the thread that
+// updates it while the others update theirs.  The Cholesky-then-triangular-
+// inverse form this replaces ran two R-long dependent chains on a few
+// threads (27 us at R = 16, 233 us at R = 64 on GB300).  zero_gram / zero_colsq (nullable): R*R
+// and R doubles cleared afterwards for this mode's update (G_n and the
+// column sums).  Shared memory: R*R doubles (M), 2R doubles (column k and
+// column k / d), R(R+1)/2 words (the pairs, i << 16 | j).
+__global__ void __launch_bounds__(512) hinv_kernel(const double *G, int d, int n, int R, float *Hinv,
+                                                   double *zero_gram, double *zero_colsq, int *status) {
     extern __shared__ double sh[];
-    double *Hs = sh;            // R x R
-    double *Wd = sh + R * R;    // R: diagonal of W
-    __shared__ int fail;
-    __shared__ double ridge;
-    const int RR = R * R;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        __syncthreads();
+    double *M = sh;           // R x R, symmetric
+    double *ck = sh + R * R;  // R: column k before step k
+    double *fk = ck + R;      // R: column k / pivot
+    uint32_t *pairs = reinterpret_cast<uint32_t *>(fk + R);
+    __shared__ double ridge, rpiv;  // rpiv: 1 / the next pivot (when it is > 0)
+    const int RR = R * R, NP = R * (R + 1) / 2;
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) {  // the pairs, row by row
+        const int i = e / R, j = e - i * R;
+        if (j >= i) pairs[i * R - i * (i - 1) / 2 + (j - i)] = ((uint32_t)i << 16) | (uint32_t)j;
+    }
+    bool ok = false;
+    for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
+        __syncthreads();  // the pairs are written; the previous attempt's readers of M are done
         for (int e = threadIdx.x; e < RR; e += blockDim.x) {
             double h = 1.0;
             for (int m = 0; m < d; ++m)
                 if (m != n) h *= G[(int64_t)m * RR + e];
-            Hs[e] = h;
+            M[e] = h;
         }
-        if (threadIdx.x == 0) fail = 0;
         __syncthreads();
         if (attempt == 1) {
             if (threadIdx.x == 0) {
                 double tr = 0.0;
-                for (int r = 0; r < R; ++r) tr += Hs[r * R + r];
+                for (int r = 0; r < R; ++r) tr += M[r * R + r];
                 ridge = 1e-12 * tr / R;
             }
             __syncthreads();
-            for (int r = threadIdx.x; r < R; r += blockDim.x) Hs[r * R + r] += ridge;
+            for (int r = threadIdx.x; r < R; r += blockDim.x) M[r * R + r] += ridge;
             __syncthreads();
         }
+        ok = true;
+        if (threadIdx.x == 0 && M[0] > 0.0) rpiv = 1.0 / M[0];
+        __syncthreads();
         for (int k = 0; k < R; ++k) {
-            if (threadIdx.x == 0) {
-                const double p = Hs[k * R + k];
-                if (!(p > 0.0)) fail = 1;
-                Hs[k * R + k] = p > 0.0 ? sqrt(p) : 1.0;
+            const double piv = M[k * R + k];  // the same value in every thread
+            if (!(piv > 0.0)) {
+                ok = false;
+                break;
+            }
+            const double rp = rpiv;
+            for (int i = threadIdx.x; i < R; i += blockDim.x) {
+                const double c = M[i * R + k];
+                ck[i] = c;
+                fk[i] = c * rp;
             }
             __syncthreads();
-            if (fail) break;
-            const double rk = 1.0 / Hs[k * R + k];  // every thread: no extra barrier
-            for (int i = k + 1 + threadIdx.x; i < R; i += blockDim.x) Hs[i * R + k] *= rk;
-            __syncthreads();
-            const int rem = R - k - 1;
-            for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-                const int i = k + 1 + e / rem, j = k + 1 + e % rem;
-                if (j <= i) Hs[i * R + j] -= Hs[i * R + k] * Hs[j * R + k];
+            for (int t = threadIdx.x; t < NP; t += blockDim.x) {
+                const uint32_t q = pairs[t];
+                const int i = (int)(q >> 16), j = (int)(q & 0xffffu);
+                double v;
+                if (i == k && j == k) v = -rp;
+                else if (i == k) v = fk[j];
+                else if (j == k) v = fk[i];
+                else v = fma(-fk[i], ck[j], M[i * R + j]);
+                M[i * R + j] = v;
+                M[j * R + i] = v;
+                if (i == k + 1 && j == k + 1 && v > 0.0) rpiv = 1.0 / v;  // read after the barrier
             }
-            __syncthreads();
+            __syncthreads();  // M and rpiv updated before the next pivot is read
         }
-        if (!fail) break;
     }
-    if (fail) {
+    if (!ok) {
         // not positive definite after the ridge: report, leave the mode's
         // factor as V (Hinv = identity)
         if (threadIdx.x == 0) atomicExch(status, SPT_DEV_SINGULAR);
         for (int e = threadIdx.x; e < RR; e += blockDim.x) Hinv[e] = (e / R == e % R) ? 1.f : 0.f;
     } else {
-        // W = L^-1 by forward substitution, one column per thread (the
-        // reciprocals of the diagonal first, so the chains carry no division)
-        for (int c = threadIdx.x; c < R; c += blockDim.x) Wd[c] = 1.0 / Hs[c * R + c];
-        __syncthreads();
-        for (int c = threadIdx.x; c < R; c += blockDim.x) {
-            for (int i = c + 1; i < R; ++i) {
-                double sacc = Hs[i * R + c] * Wd[c];
-                for (int k = c + 1; k < i; ++k) sacc += Hs[i * R + k] * Hs[c * R + k];
-                Hs[c * R + i] = -sacc * Wd[i];  // W[i][c] stored at (c, i)
-            }
-        }
-        __syncthreads();
-        // Hinv(i,j) = sum_{k >= max(i,j)} W[k][i] W[k][j]
-        for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-            const int i = e / R, j = e % R;
-            const int k0 = i > j ? i : j;
-            double sacc = 0.0;
-            for (int k = k0; k < R; ++k) {
-                const double wi = (k == i) ? Wd[i] : Hs[i * R + k];
-                const double wj = (k == j) ? Wd[j] : Hs[j * R + k];
-                sacc += wi * wj;
-            }
-            Hinv[e] = (float)sacc;
-        }
+        for (int e = threadIdx.x; e < RR; e += blockDim.x) Hinv[e] = (float)(-M[e]);
     }
     __syncthreads();  // every thread has read G before G_n is cleared
     if (zero_gram)
         for (int e = threadIdx.x; e < RR; e += blockDim.x) zero_gram[e] = 0.0;
     if (zero_colsq)
         for (int r = threadIdx.x; r < R; r += blockDim.x) zero_colsq[r] = 0.0;
+}
+
+// Threads of a hinv_kernel launch: one per pair up to 512, whole warps.
+inline int hinv_threads(int R) { return std::min(512, std::max(32, (R * (R + 1) / 2 + 31) / 32 * 32)); }
+inline size_t hinv_smem(int R) {
+    return sizeof(double) * ((size_t)R * R + 2 * (size_t)R) + sizeof(uint32_t) * ((size_t)R * (R + 1) / 2);
 }
 
 // A32 = V Hinv, column sums of squares.  Thread (rq, cq) computes the 4 x 4
@@ -478,6 +526,7 @@ __global__ void fit_kernel(const double *G, int d, int R, const double *lambda, 
 struct Ws {
     float *V, *A32, *Hinv;
     double *G, *colsq, *inner;
+    double *Gp;  // partial Grams of the two-stage reduction
     int *status;
 };
 
@@ -497,6 +546,7 @@ size_t ws_layout(spt_tensor t, int R, int ld, Ws *w, void *base) {
     const size_t oG = take(sizeof(double) * t->d * R * R);
     const size_t oC = take(sizeof(double) * R);
     const size_t oI = take(sizeof(double));
+    const size_t oP = take(sizeof(double) * (size_t)sm_count() * gram_ctas_per_sm(R) * R * R);
     if (w && base) {
         char *b = (char *)base;
         w->V = (float *)(b + oV);
@@ -505,26 +555,49 @@ size_t ws_layout(spt_tensor t, int R, int ld, Ws *w, void *base) {
         w->G = (double *)(b + oG);
         w->colsq = (double *)(b + oC);
         w->inner = (double *)(b + oI);
+        w->Gp = (double *)(b + oP);
         w->status = (int *)(b + oS);
     }
     return off;
 }
 
+// G += A^T A.  With `partials` (room for sm_count() * gram_ctas_per_sm(R)
+// R x R blocks) each CTA stores its sum there and a second kernel adds them
+// in block order, so no FP64 atomics pile up on the R x R entries (the
+// first form measured ~28 us of fixed cost on 608 CTAs at R = 16); without
+// it each CTA adds its sum atomically.
 template <typename FT>
-spt_status launch_gram(const void *A, int64_t I, int ld, int R, double *G, cudaStream_t st) {
+spt_status launch_gram(const void *A, int64_t I, int ld, int R, double *G, double *partials, cudaStream_t st) {
     const GramShape g = gram_shape(R, (int)sizeof(FT));
     const int64_t tiles = (I + g.tile_rows - 1) / g.tile_rows;
-    const int blocks = (int)std::max<int64_t>(
-        1, std::min<int64_t>(tiles, (int64_t)sm_count() * std::max(1, 1024 / g.threads)));
-    gram_kernel<FT><<<blocks, g.threads, g.smem, st>>>((const FT *)A, I, ld, R, G);
+    int bps = 0;
+    SPT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, gram_kernel<FT>, g.threads, g.smem));
+    bps = std::max(1, std::min(bps, gram_ctas_per_sm(R)));
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sm_count() * bps));
+    gram_kernel<FT><<<blocks, g.threads, g.smem, st>>>((const FT *)A, I, ld, R, G, partials);
     SPT_LAUNCH_CHECK("gram_kernel");
+    if (partials) {
+        gram_reduce_kernel<<<(R * R + 7) / 8, 256, 0, st>>>(partials, blocks, R * R, G);
+        SPT_LAUNCH_CHECK("gram_reduce_kernel");
+    }
     return SPT_OK;
 }
 
-spt_status gram_any(spt_dtype fdt, const void *A, int64_t I, int ld, int R, double *G, cudaStream_t st) {
-    if (fdt == SPT_F32) return launch_gram<float>(A, I, ld, R, G, st);
-    if (fdt == SPT_BF16) return launch_gram<__nv_bfloat16>(A, I, ld, R, G, st);
-    return launch_gram<__half>(A, I, ld, R, G, st);
+spt_status gram_any(spt_dtype fdt, const void *A, int64_t I, int ld, int R, double *G, double *partials,
+                    cudaStream_t st) {
+    if (fdt == SPT_F32) return launch_gram<float>(A, I, ld, R, G, partials, st);
+    if (fdt == SPT_BF16) return launch_gram<__nv_bfloat16>(A, I, ld, R, G, partials, st);
+    return launch_gram<__half>(A, I, ld, R, G, partials, st);
+}
+
+// CTAs of a solve launch over I rows in tiles of trows: as many as fit on
+// the GPU at once (each keeps one tile load in flight; two CTAs per SM left
+// the apply at ~40% of the copy bandwidth on 1e6 x 16 rows).
+spt_status solve_grid(int64_t I, int trows, size_t smem, int *blocks) {
+    int bps = 0;
+    SPT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, solve_kernel, 256, smem));
+    *blocks = (int)std::max<int64_t>(1, std::min<int64_t>((I + trows - 1) / trows, (int64_t)sm_count() * std::max(1, bps)));
+    return SPT_OK;
 }
 
 // Dynamic shared-memory limits of the CP-ALS kernels, once per device.
@@ -536,8 +609,7 @@ spt_status ensure_cpals_attrs() {
     if (dev < 0 || dev >= 64) dev = 0;
     std::lock_guard<std::mutex> lk(mu);
     if (done[dev]) return SPT_OK;
-    SPT_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  sizeof(double) * (MAXR * MAXR + MAXR)));
+    SPT_CUDA(cudaFuncSetAttribute(hinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hinv_smem(MAXR)));
     size_t ssm = 0;
     for (int r = 1; r <= MAXR; ++r) {
         const int ct = (r + 3) / 4, tr = 4 * (256 / ct);
@@ -564,23 +636,28 @@ spt_status enqueue_step(spt_tensor t, void *const *factors, spt_dtype fdt, int R
     SPT_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * d * R * R, st));
     SPT_CUDA(cudaMemsetAsync(w.inner, 0, sizeof(double), st));
     SPT_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), st));
-    for (int m = 0; m < d; ++m) {
-        spt_status s = gram_any(fdt, factors[m], t->dims[m], ld, R, w.G + (size_t)m * R * R, st);
+    // the Grams the first mode's H needs (G_0 itself is first needed after
+    // mode 0's update, which recomputes it)
+    for (int m = 1; m < d; ++m) {
+        spt_status s = gram_any(fdt, factors[m], t->dims[m], ld, R, w.G + (size_t)m * R * R, w.Gp, st);
         if (s) return s;
     }
-    const size_t chol_smem = sizeof(double) * (R * R + R);
     for (int n = 0; n < d; ++n) {
         const int64_t In = t->dims[n];
         spt_schedule sc = default_schedule(t, n, fdt, R);
         spt_status s = launch_mttkrp(t, n, factors, fdt, R, ld, nullptr, w.V, sc, st);
         if (s) return s;
-        chol_inv_kernel<<<1, 512, chol_smem, st>>>(w.G, d, n, R, w.Hinv, w.G + (size_t)n * R * R, w.colsq,
+        hinv_kernel<<<1, hinv_threads(R), hinv_smem(R), st>>>(w.G, d, n, R, w.Hinv, w.G + (size_t)n * R * R, w.colsq,
                                                    w.status);
-        SPT_LAUNCH_CHECK("chol_inv_kernel");
+        SPT_LAUNCH_CHECK("hinv_kernel");
         const int CT = (R + 3) / 4;
         const int trows = 4 * (256 / CT);
         const size_t solve_smem = sizeof(float) * ((size_t)R * CT * 4 + (size_t)2 * trows * (CT * 4 + 4));
-        const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((In + trows - 1) / trows, sm_count() * 2));
+        int sblocks = 0;
+        {
+            spt_status e = solve_grid(In, trows, solve_smem, &sblocks);
+            if (e) return e;
+        }
         solve_kernel<<<sblocks, 256, solve_smem, st>>>(w.V, In, ld, R, w.Hinv, w.A32, w.colsq);
         SPT_LAUNCH_CHECK("solve_kernel");
         const int rpp = std::max(1, 256 / (ld / 4));  // rows per pass of a 256-thread block
@@ -596,7 +673,7 @@ spt_status enqueue_step(spt_tensor t, void *const *factors, spt_dtype fdt, int R
             normalize_kernel<__half><<<nblocks, 256, 0, st>>>(w.A32, w.V, In, ld, R, w.colsq,
                                                               (__half *)factors[n], lambda, last, w.inner);
         SPT_LAUNCH_CHECK("normalize_kernel");
-        s = gram_any(fdt, factors[n], In, ld, R, w.G + (size_t)n * R * R, st);
+        s = gram_any(fdt, factors[n], In, ld, R, w.G + (size_t)n * R * R, w.Gp, st);
         if (s) return s;
     }
     fit_kernel<<<1, 256, 0, st>>>(w.G, d, R, lambda, w.inner, t->xnorm2, fit_out);
@@ -703,9 +780,9 @@ spt_status cp_als_hinv(const double *G, int order, int mode, int rank, float *hi
     spt_status a = ensure_cpals_attrs();
     if (a) return a;
     cudaStream_t st = (cudaStream_t)stream;
-    chol_inv_kernel<<<1, 512, sizeof(double) * (rank * rank + rank), st>>>(G, order, mode, rank, hinv, nullptr,
-                                                                             nullptr, status);
-    SPT_LAUNCH_CHECK("chol_inv_kernel");
+    hinv_kernel<<<1, hinv_threads(rank), hinv_smem(rank), st>>>(G, order, mode, rank, hinv, nullptr, nullptr,
+                                                                 status);
+    SPT_LAUNCH_CHECK("hinv_kernel");
     return SPT_OK;
 }
 
@@ -722,7 +799,11 @@ spt_status cp_als_apply(const float *V, int64_t rows, int ld, int rank, const fl
     const int CT = (rank + 3) / 4;
     const int trows = 4 * (256 / CT);
     const size_t smem = sizeof(float) * ((size_t)rank * CT * 4 + (size_t)2 * trows * (CT * 4 + 4));
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + trows - 1) / trows, sm_count() * 2));
+    int blocks = 0;
+    {
+        spt_status e = solve_grid(rows, trows, smem, &blocks);
+        if (e) return e;
+    }
     solve_kernel<<<blocks, 256, smem, st>>>(V, rows, ld, rank, hinv, A32, colsq);
     SPT_LAUNCH_CHECK("solve_kernel");
     return SPT_OK;
@@ -763,7 +844,7 @@ spt_status cp_als_gram(const void *A, int64_t rows, int ld, int rank, spt_dtype 
     spt_status a = ensure_cpals_attrs();
     if (a) return a;
     if (rows == 0) return SPT_OK;
-    return gram_any(fdt, A, rows, ld, rank, G, (cudaStream_t)stream);
+    return gram_any(fdt, A, rows, ld, rank, G, nullptr, (cudaStream_t)stream);
 }
 
 spt_status cp_als_fit(const double *G, int order, int rank, const double *lambda, double *inner, double xnorm2,
