@@ -55,6 +55,8 @@
 //    c starts at column rb*L*C*VEC + (c*L + l)*VEC.  Columns >= R are
 //    computed from the factors' padding and written as zeros.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace spt {
@@ -131,6 +133,28 @@ __device__ __forceinline__ void red_add4(double *dst, const double *v) {
     for (int q = 0; q < 4; ++q) atomicAdd(dst + q, v[q]);
 }
 __device__ __forceinline__ float fma_acc(float a, float b, float c) { return fmaf(a, b, c); }
+
+// Two fp32 multiplies / FMAs in one packed instruction (mul / fma .rn.f32x2,
+// sm_100 and later); each half rounds exactly as the scalar operation, so
+// results are bit-identical to the scalar form.  Measured on the sorted
+// traversal: 3-way fp32 R=16 +2.7%, 4-way bf16 R=64 +2.3%, 4-way fp32 R=64
+// -2.2% (there the scalar form stays).  0 turns it off everywhere.
+#ifndef SPT_PACKED_FMA
+#define SPT_PACKED_FMA 1
+#endif
+__device__ __forceinline__ void mul2(float &d0, float &d1, float a0, float a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "mul.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void fma2(float &d0, float &d1, float a0, float a1, float b0, float b1, float c0,
+                                     float c1) {
+    asm("{\n\t.reg .b64 pa, pb, pc, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "mov.b64 pc, {%6, %7};\n\tfma.rn.f32x2 pd, pa, pb, pc;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1), "f"(c0), "f"(c1));
+}
 __device__ __forceinline__ double fma_acc(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ void store4(float *dst, const float *v) {
     *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
@@ -220,6 +244,10 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
     constexpr int LOADS = NR * C;
     constexpr int U = (LOADS <= 2) ? 2 : 1;
     constexpr unsigned FULL = 0xffffffffu;
+    // packed fp32 products (fp32 accumulators; 16-bit factors, or fp32 ones of
+    // orders <= 3); bit-identical to the scalar form
+    constexpr bool PACKED = SPT_PACKED_FMA && std::is_same<AT, float>::value && VEC % 2 == 0 &&
+                            (E::BYTES == 2 || D1 <= 2);
     const int lane = threadIdx.x & 31;
     const int npw = p.npw;
     const int log2L = p.log2L;
@@ -448,8 +476,14 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
                 for (int m = 0; m + 1 < D1; ++m) {
                     AT f[VEC];
                     E::widen(rw[m][c], f);
+                    if constexpr (PACKED) {
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) part[c][v] *= f[v];
+                        for (int v = 0; v < VEC; v += 2)
+                            mul2(part[c][v], part[c][v + 1], part[c][v], part[c][v + 1], f[v], f[v + 1]);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) part[c][v] *= f[v];
+                    }
                 }
                 if (D1 > 0) E::widen(rw[DA - 1][c], fl[c]);
             }
@@ -472,18 +506,35 @@ __device__ __forceinline__ void mttkrp_chunk(const MttkrpParams &p, const int32_
                     }
                 }
                 cur = row;
+                if constexpr (PACKED && D1 > 0) {
 #pragma unroll
-                for (int c = 0; c < C; ++c)
+                    for (int c = 0; c < C; ++c)
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v)
-                        acc[c][v] = D1 > 0 ? part[c][v] * fl[c][v] : part[c][v];
+                        for (int v = 0; v < VEC; v += 2)
+                            mul2(acc[c][v], acc[c][v + 1], part[c][v], part[c][v + 1], fl[c][v], fl[c][v + 1]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v)
+                            acc[c][v] = D1 > 0 ? part[c][v] * fl[c][v] : part[c][v];
+                }
             } else {
+                if constexpr (PACKED && D1 > 0) {
 #pragma unroll
-                for (int c = 0; c < C; ++c)
+                    for (int c = 0; c < C; ++c)
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v)
-                        acc[c][v] = D1 > 0 ? fma_acc(part[c][v], fl[c][v], acc[c][v])
-                                           : acc[c][v] + part[c][v];
+                        for (int v = 0; v < VEC; v += 2)
+                            fma2(acc[c][v], acc[c][v + 1], part[c][v], part[c][v + 1], fl[c][v], fl[c][v + 1],
+                                 acc[c][v], acc[c][v + 1]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v)
+                            acc[c][v] = D1 > 0 ? fma_acc(part[c][v], fl[c][v], acc[c][v])
+                                               : acc[c][v] + part[c][v];
+                }
             }
         };
 
