@@ -725,8 +725,10 @@ def measure_extras(args, P, torch, w, T, idx, vals, facs_np, dtype, R, d, ld, ou
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(side)
         iters = 5
+        torch.cuda.nvtx.range_push("cpals")  # the timed iterations' launches (ncu --nvtx-include cpals/)
         for _ in range(iters):
             Tc.cp_als_step(fc, R, lam, fit, ws)
+        torch.cuda.nvtx.range_pop()
         e1.record(side)
     torch.cuda.synchronize()
     it_ms = e0.elapsed_time(e1) / iters
