@@ -1106,9 +1106,10 @@ def run_paper_sweep(args):
 
 def run_shard_cpals(args):
     """CP-ALS with the nonzeros split across the ranks (one per GPU, NCCL):
-    every rank holds a contiguous range of each mode's permutation, V is
-    reduce-scattered by row blocks, the Grams and column norms all-reduced,
-    the factor rows all-gathered (paper Sec. 8 future work).  The workload's
+    every rank holds a contiguous range of each mode's permutation and owns
+    the rows it reaches first; the rows shared at the cuts are completed by
+    one small all-reduce, the Grams and column norms all-reduced, and each
+    rank's factor rows broadcast (paper Sec. 8 future work).  The workload's
     tensor is coalesced; `--shard-cpals K` timed iterations after --warmup,
     the slowest rank's time.  With one rank, cp_als_step on the same GPU is
     timed beside it (the cost of the split and of the collectives' calls)."""
@@ -1143,7 +1144,7 @@ def run_shard_cpals(args):
     tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[fdt]
     facs = [torch.from_numpy(f.view(np.int16) if fdt != "f32" else f).cuda().view(tdt) for f in facs_np]
     drv = S.ShardedCPALS(S.DeviceOps(T, shards, R, fdt, ld), w.dims, R, ld)
-    F = drv.padded_factors(facs)
+    F = drv.replicated_factors(facs)
     lam = torch.zeros(R, dtype=torch.float64, device="cuda")
     fit = torch.zeros(1, dtype=torch.float64, device="cuda")
     for _ in range(args.warmup):
@@ -1162,13 +1163,13 @@ def run_shard_cpals(args):
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms = float(t.item())
     s_f = 4 if fdt == "f32" else 2
-    comm = sum(S.row_block(I, world) * world * ld * (4 + s_f) for I in w.dims) + (2 * d + 1) * R * R * 8
+    comm = drv.collective_bytes(s_f)
     line = {"metric": "sharded CP-ALS iter/s", "workload": w.name, "n_gpus": world, "nnz_coalesced": T.nnz,
             "R": R, "factors": fdt, "iterations": args.shard_cpals, "warmup": args.warmup,
             "ms_per_iter": ms, "iter_per_s": 1e3 / ms, "fit": float(fit.item()),
             "collective_bytes_per_rank_per_iter": comm,
-            "collectives": "per mode: reduce-scatter of V (fp32), all-reduce of the column norms and of "
-                           "the R x R FP64 Gram, all-gather of the factor rows"}
+            "collectives": "per mode: all-reduce of the rows shared at the cuts (world x ld fp32), of the "
+                           "column norms and of the R x R FP64 Gram, one broadcast of each rank's factor rows"}
     if world == 1:  # the unsplit iteration on the same GPU
         g = [torch.from_numpy(f.view(np.int16) if fdt != "f32" else f).cuda().view(tdt) for f in facs_np]
         ws = T.cp_als_workspace(R, ld)

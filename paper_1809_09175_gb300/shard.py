@@ -3,27 +3,37 @@
 names as its first piece of future work (Sec. 8).
 
 Every rank holds, for each mode n, the nonzeros at one contiguous range of
-the mode-n permutation (``tensor_create_shard``), so its rows of V are mostly
-its own, and a full copy of every factor matrix.  One mode update:
+the mode-n permutation (``tensor_create_shard``), and a full copy of every
+factor matrix.  The permutation is sorted by the mode-n coordinate, so a
+rank's nonzeros cover one run of rows [first_r, last_r], and two ranks share
+at most the row at the cut between them.  Rank r owns the rows after the
+previous ranks' last rows up to its own last row (the last rank also owns
+the rows after it, which hold no nonzeros), so every row has one owner and a
+shared row belongs to the lowest rank whose nonzeros reach it.  One mode update:
 
-1. partial V = the mode-n MTTKRP of the rank's nonzeros (all I_n rows);
-2. **reduce-scatter** of V by row blocks: rank r receives the summed rows
-   ``[r B, (r+1) B)``, ``B = ceil(I_n / G)`` (V padded to ``G B`` rows);
-3. ``H^-1`` from the replicated FP64 Grams, ``A32 = V_r H^-1`` on the rank's
+1. partial V = the mode-n MTTKRP of the rank's nonzeros;
+2. the **boundary rows**: each rank puts its partial of the row it shares
+   with a lower rank into that owner's slot of a G x ld buffer, and its own
+   last row into its slot; one **all-reduce** of that buffer, and each owner
+   takes its slot back as the full row of V.  No other row of V has a
+   partial on another rank, so V is never reduced as a whole;
+3. ``H^-1`` from the replicated FP64 Grams, ``A32 = V_r H^-1`` on the owned
    rows and their column sums of squares, **all-reduced** into lambda;
-4. the normalised rows ``A_r = A32 / lambda``, their Gram ``A_r^T A_r``
-   **all-reduced** into G_n (R x R FP64);
-5. **all-gather** of the rows ``A_r`` into the replicated ``A^(n)``.
+4. the normalised rows ``A_r = A32 / lambda`` written into the rank's rows
+   of the factor, their Gram ``A_r^T A_r`` **all-reduced** into G_n;
+5. one **broadcast** per rank of its rows of the factor.
 
-After the last mode the fit's ``<X, M>`` (from the last V's rows) and, once,
-``||X||^2`` (from the mode-0 shards) are all-reduced.  The steps of 1 and
-3-5 run in the library's CUDA kernels through the C ABI (:class:`DeviceOps`);
-this module only moves buffers between them and the collectives.  The
-collectives are ``torch.distributed`` calls (NCCL between GPUs).
+Per mode a rank then sends its rows of the new factor and R + R^2 + G ld
+numbers, where a reduce-scatter of V by row blocks would also move I_n x R
+fp32 partial sums.  After the last mode the fit's ``<X, M>`` (from the owned
+rows of the last V) and, once, ``||X||^2`` (from the mode-0 shards) are
+all-reduced.  The steps of 1 and 3-4 run in the library's CUDA kernels
+through the C ABI (:class:`DeviceOps`); this module only moves buffers
+between them and the collectives (``torch.distributed``, NCCL between GPUs).
 """
 from __future__ import annotations
 
-from typing import List, Optional, Sequence
+from typing import List, Optional, Sequence, Tuple
 
 import torch
 import torch.distributed as dist
@@ -38,10 +48,30 @@ def shard_bounds(nnz: int, world: int, rank: int):
     return nnz * rank // world, nnz * (rank + 1) // world
 
 
-def row_block(I: int, world: int):
-    """Rows per rank of the reduce-scatter (V and the factors are padded to
-    ``world * B`` rows)."""
-    return (I + world - 1) // world
+def owned_rows(lasts: Sequence[int], I: int) -> List[Tuple[int, int]]:
+    """Row range ``[lo, hi)`` of every rank from the ranks' last rows in rank
+    order (-1 for a rank without nonzeros): rank r owns the rows after the
+    largest last row of the ranks before it, up to and including its own
+    last row; the last rank also owns the rows up to I.  A rank whose
+    nonzeros all lie in a row owned by a lower rank owns nothing (lo == hi)."""
+    out = []
+    prev = -1
+    G = len(lasts)
+    for r in range(G):
+        cur = max(prev, int(lasts[r]))
+        lo = prev + 1
+        hi = I if r == G - 1 else cur + 1
+        out.append((lo, max(lo, hi)))
+        prev = cur
+    return out
+
+
+def row_owner(own: Sequence[Tuple[int, int]], row: int) -> int:
+    """The rank whose range of ``own`` holds ``row``."""
+    for r, (lo, hi) in enumerate(own):
+        if lo <= row < hi:
+            return r
+    raise ValueError(f"row {row} is outside every rank's range")
 
 
 class DeviceOps:
@@ -63,11 +93,19 @@ class DeviceOps:
     def _s() -> int:
         return torch.cuda.current_stream().cuda_stream
 
+    def row_span(self, mode: int) -> Tuple[int, int]:
+        """First and last mode-n row of this rank's mode-n shard, (-1, -1)
+        if it holds no nonzeros (the shard keeps the permutation's order, so
+        they are its first and last coordinates)."""
+        S = self.shards[mode]
+        if S.nnz == 0:
+            return -1, -1
+        idx, _ = S.coo()
+        return int(idx[mode, 0].item()), int(idx[mode, -1].item())
+
     def partial_mttkrp(self, mode: int, factors: List[torch.Tensor], V: torch.Tensor):
-        """V[:I_n] = MTTKRP of this rank's mode-n shard (rows past I_n zero)."""
-        I = self.T.dims[mode]
-        V[I:].zero_()
-        self.shards[mode].mttkrp(mode, factors, self.R, out=V[:I])
+        """V (I_n rows) = MTTKRP of this rank's mode-n shard."""
+        self.shards[mode].mttkrp(mode, factors, self.R, out=V)
 
     def gram(self, A: torch.Tensor, rows: int, G: torch.Tensor):
         G.zero_()
@@ -119,9 +157,8 @@ class ShardedCPALS:
     """CP-ALS iterations over nonzeros split across a process group.
 
     ``ops`` performs the rank's local steps (:class:`DeviceOps` on a GPU);
-    ``factors`` are the replicated factor matrices (I_m x ld each, padded
-    here to ``world * B_m`` rows so that the collectives see equal blocks).
-    All collective arguments are torch tensors on the ops' device."""
+    ``factors`` are the replicated factor matrices (I_m x ld each).  All
+    collective arguments are torch tensors on the ops' device."""
 
     def __init__(self, ops, dims: Sequence[int], rank_: int, ld: int, group=None):
         self.ops = ops
@@ -133,51 +170,76 @@ class ShardedCPALS:
         self.world = dist.get_world_size(group)
         self.rank = dist.get_rank(group)
         self.x2 = None
+        self.spans = None  # per mode: every rank's (first, last) row
+        self.own = None    # per mode: every rank's owned rows [lo, hi)
 
-    def _pad(self, I: int) -> int:
-        return self.world * row_block(I, self.world)
+    def replicated_factors(self, factors: Sequence[torch.Tensor]) -> List[torch.Tensor]:
+        """Copies of the factors for the iteration to update in place."""
+        return [f.clone() for f in factors]
 
-    def padded_factors(self, factors: Sequence[torch.Tensor]) -> List[torch.Tensor]:
-        """Copies of the factors padded with zero rows to world * B_m rows (the
-        iteration updates them in place; row I_m and beyond stay zero)."""
-        out = []
-        for m, f in enumerate(factors):
-            p = torch.zeros((self._pad(self.dims[m]), f.shape[1]), dtype=f.dtype, device=f.device)
-            p[: self.dims[m]].copy_(f)
-            out.append(p)
-        return out
+    def _partition(self, dev):
+        """Every rank's row span and owned rows of every mode (once: the
+        shards do not change between iterations)."""
+        if self.own is not None:
+            return
+        mine = torch.tensor([v for n in range(self.d) for v in self.ops.row_span(n)], dtype=torch.int64,
+                            device=dev)
+        every = [torch.empty_like(mine) for _ in range(self.world)]
+        dist.all_gather(every, mine, group=self.group)
+        every = [e.cpu().tolist() for e in every]
+        self.spans = [[(e[2 * n], e[2 * n + 1]) for e in every] for n in range(self.d)]
+        self.own = [owned_rows([sp[1] for sp in self.spans[n]], self.dims[n]) for n in range(self.d)]
+
+    def _boundary_rows(self, n: int, V: torch.Tensor):
+        """Complete the rows of V that a rank shares with the rank owning
+        them: one all-reduce of a world x ld buffer (step 2)."""
+        w, r = self.world, self.rank
+        own, (first, last) = self.own[n], self.spans[n][r]
+        lo, hi = own[r]
+        Z = torch.zeros((w, V.shape[1]), dtype=V.dtype, device=V.device)
+        owns_last = first >= 0 and lo <= last < hi
+        if owns_last:
+            Z[r].copy_(V[last])
+        if first >= 0:
+            o = row_owner(own, first)
+            if o != r:
+                Z[o].copy_(V[first])
+        dist.all_reduce(Z, group=self.group)
+        if owns_last:
+            V[last].copy_(Z[r])
 
     def step(self, F: List[torch.Tensor], lam: torch.Tensor, fit: Optional[torch.Tensor] = None):
-        """One iteration over every mode in order; F are the padded factors
-        (updated in place), lam receives lambda (rank doubles)."""
+        """One iteration over every mode in order; F are the replicated
+        factors (updated in place), lam receives lambda (rank doubles)."""
         dev = F[0].device
         f64 = dict(dtype=torch.float64, device=dev)
         d, R, ld, w, r = self.d, self.R, self.ld, self.world, self.rank
+        self._partition(dev)
         Grams = torch.zeros((d, R, R), **f64)
-        for m in range(d):  # each rank's rows, summed over the ranks
-            Bm = row_block(self.dims[m], w)
-            rows = max(0, min(Bm, self.dims[m] - r * Bm))
-            self.ops.gram(F[m][r * Bm:], rows, Grams[m])
+        for m in range(d):  # each rank's owned rows, summed over the ranks
+            lo, hi = self.own[m][r]
+            self.ops.gram(F[m][lo:hi], hi - lo, Grams[m])
         dist.all_reduce(Grams, group=self.group)
         colsq = torch.zeros(R, **f64)
         inner = torch.zeros(1, **f64)
         for n in range(d):
-            In = self.dims[n]
-            Bn = row_block(In, w)
-            rows = max(0, min(Bn, In - r * Bn))
-            V = torch.empty((w * Bn, ld), dtype=self.ops.acc_dtype, device=dev)
+            lo, hi = self.own[n][r]
+            rows = hi - lo
+            V = torch.empty((self.dims[n], ld), dtype=self.ops.acc_dtype, device=dev)
             self.ops.partial_mttkrp(n, [f[: self.dims[m]] for m, f in enumerate(F)], V)
-            Vr = torch.empty((Bn, ld), dtype=self.ops.acc_dtype, device=dev)
-            dist.reduce_scatter_tensor(Vr, V, group=self.group)
-            A32 = torch.zeros((Bn, ld), dtype=self.ops.acc_dtype, device=dev)
+            self._boundary_rows(n, V)
+            Vr = V[lo:hi]
+            A32 = torch.zeros((max(rows, 1), ld), dtype=self.ops.acc_dtype, device=dev)
             self.ops.solve_rows(n, Grams, Vr, rows, A32, colsq)
             dist.all_reduce(colsq, group=self.group)
-            Ar = torch.zeros((Bn, ld), dtype=F[n].dtype, device=dev)
+            Ar = F[n][lo:hi]  # the rank's rows of the factor, written in place
             last = n == d - 1
             self.ops.normalize_rows(A32, rows, colsq, Ar, lam, Vr if last else None, inner if last else None)
             self.ops.gram(Ar, rows, Grams[n])
             dist.all_reduce(Grams[n], group=self.group)
-            dist.all_gather_into_tensor(F[n], Ar, group=self.group)
+            for s, (slo, shi) in enumerate(self.own[n]):
+                if shi > slo:
+                    dist.broadcast(F[n][slo:shi], src=s, group=self.group)
         dist.all_reduce(inner, group=self.group)
         if self.x2 is None:
             x2 = torch.tensor([self.ops.xnorm2()], **f64)
@@ -188,5 +250,14 @@ class ShardedCPALS:
         self.ops.check()
         return Grams
 
+    def collective_bytes(self, factor_bytes: int) -> int:
+        """Bytes one iteration's collectives carry per rank (the sizes passed
+        to them; needs a completed step): the boundary-row buffers, the
+        broadcast factor rows, column norms, Grams and the two scalars."""
+        acc = torch.tensor([], dtype=self.ops.acc_dtype).element_size()
+        R, w, ld = self.R, self.world, self.ld
+        per_mode = sum(w * ld * acc + I * ld * factor_bytes + R * 8 + R * R * 8 for I in self.dims)
+        return per_mode + self.d * R * R * 8 + 8
 
-__all__ = ["DeviceOps", "ShardedCPALS", "make_shards", "shard_bounds", "row_block"]
+
+__all__ = ["DeviceOps", "ShardedCPALS", "make_shards", "shard_bounds", "owned_rows", "row_owner"]

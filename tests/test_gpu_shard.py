@@ -80,7 +80,7 @@ def test_one_rank_sharded_iteration_matches_oracle_and_cp_als_step(nccl_one_rank
     facs = [to_device_factor(f, dtype) for f in facs_np]
     ld = facs[0].shape[1]
     drv = S.ShardedCPALS(S.DeviceOps(T, shards, R, dtype, ld), dims, R, ld)
-    F = drv.padded_factors(facs)
+    F = drv.replicated_factors(facs)
     lam = torch.zeros(R, dtype=torch.float64, device="cuda")
     fit = torch.zeros(1, dtype=torch.float64, device="cuda")
     drv.step(F, lam, fit)

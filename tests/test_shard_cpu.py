@@ -1,9 +1,11 @@
-"""World-size-2 gloo tests of the nonzero-sharded CP-ALS (CPU only).
+"""gloo tests of the nonzero-sharded CP-ALS on two and three ranks (CPU only).
 
 The distribution of ``paper_1809_09175_gb300.shard`` -- every rank holds a
-contiguous range of each mode's permutation, partial V reduce-scattered by
-row blocks, the rank's rows solved, the column norms and the R x R Grams
-all-reduced, the factor rows all-gathered -- runs here on two gloo ranks.
+contiguous range of each mode's permutation and owns the rows it reaches
+first, the rows shared at the cuts completed by one small all-reduce, the
+owned rows solved, the column norms and the R x R Grams all-reduced, each
+rank's factor rows broadcast -- runs here on gloo ranks, including a case
+whose hot rows span whole ranks (ranks that own no row of a mode).
 The rank-local steps that run in CUDA kernels on a GPU are done in FP64 on
 the host: the MTTKRP of the rank's nonzeros by the oracle, the small dense
 steps by numpy.  One sharded iteration must then reproduce the oracle's
@@ -33,9 +35,17 @@ def _case(name):
     if name == "zipf3":
         dims, R = (41, 37, 29), 5
         idx, vals = synth.coo_zipf(dims, 3000, 0.9, 17)
-    else:  # a 4-way tensor with a mode shorter than the world's row blocks would like
+    elif name == "zipf4_short_mode":  # a 4-way tensor with a 3-row mode
         dims, R = (23, 3, 19, 11), 4
         idx, vals = synth.coo_zipf(dims, 1500, 0.6, 18)
+    else:  # mode-0 row 7 holds 1200 of 1500 draws (about 3/4 of the coalesced
+        # nonzeros), so on three ranks the middle rank's range lies inside it
+        # and that rank owns no row of mode 0
+        dims, R = (30, 40, 35), 4
+        rng = np.random.default_rng(19)
+        idx = np.stack([np.where(np.arange(1500) < 1200, 7, rng.integers(0, dims[0], 1500)),
+                        rng.integers(0, dims[1], 1500), rng.integers(0, dims[2], 1500)]).astype(np.int32)
+        vals = rng.random(1500).astype(np.float32)
     import oracle
     idx, vals = oracle.coalesce(idx, vals)
     return dims, R, idx, vals.astype(np.float64)
@@ -49,6 +59,12 @@ class HostOps:
 
     def __init__(self, dims, R, shards):
         self.dims, self.R, self.shards = dims, R, shards
+
+    def row_span(self, mode):
+        idx, _ = self.shards[mode]
+        if idx.shape[1] == 0:
+            return -1, -1
+        return int(idx[mode, 0]), int(idx[mode, -1])
 
     def partial_mttkrp(self, mode, factors, V):
         import oracle
@@ -113,23 +129,23 @@ def _worker(rank, world, port, out_dir, name):
     ld = synth.padded_ld(R)
     facs = [torch.from_numpy(f.astype(np.float64)) for f in synth.factor_matrices(dims, R, 5, "uniform")]
     drv = S.ShardedCPALS(HostOps(dims, R, shards), dims, R, ld)
-    F = drv.padded_factors(facs)
+    F = drv.replicated_factors(facs)
     lam = torch.zeros(R, dtype=torch.float64)
     fit = torch.zeros(1, dtype=torch.float64)
     drv.step(F, lam, fit)
     np.savez(os.path.join(out_dir, f"r{rank}.npz"), lam=lam.numpy(), fit=fit.numpy(),
-             **{f"A{m}": F[m][: dims[m], :R].numpy() for m in range(len(dims))},
-             **{f"P{m}": F[m][dims[m]:].numpy() for m in range(len(dims))})
+             **{f"A{m}": F[m][:, :R].numpy() for m in range(len(dims))},
+             **{f"P{m}": F[m][:, R:].numpy() for m in range(len(dims))},
+             own=np.array([[lo, hi] for n in range(len(dims)) for lo, hi in drv.own[n]]))
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("name", ["zipf3", "zipf4_short_mode"])
-def test_two_gloo_ranks_match_one_oracle_iteration(tmp_path, name):
+@pytest.mark.parametrize("name,world", [("zipf3", 2), ("zipf4_short_mode", 2), ("hot_rows", 3)])
+def test_gloo_ranks_match_one_oracle_iteration(tmp_path, name, world):
     import sys
     sys.path.insert(0, ROOT)
     import oracle
     import synth
-    world = 2
     mp.spawn(_worker, args=(world, _free_port(), str(tmp_path), name), nprocs=world, join=True)
     dims, R, idx, vals = _case(name)
     A = [f[:, :R].astype(np.float64).copy() for f in synth.factor_matrices(dims, R, 5, "uniform")]
@@ -139,12 +155,15 @@ def test_two_gloo_ranks_match_one_oracle_iteration(tmp_path, name):
         z = np.load(tmp_path / f"r{r}.npz")
         for m in range(len(dims)):  # replicated factors, equal to the oracle's
             np.testing.assert_allclose(z[f"A{m}"], A[m], rtol=1e-10, atol=1e-12)
-            assert not z[f"P{m}"].any()  # the padding rows stay zero
+            assert not z[f"P{m}"].any()  # the padding columns stay zero
         np.testing.assert_allclose(z["lam"], lam_o, rtol=1e-10)
         assert abs(float(z["fit"][0]) - fit_o) <= 1e-10
+    if name == "hot_rows":  # the middle rank owns no row of mode 0
+        own = np.load(tmp_path / "r0.npz")["own"]
+        assert own[1][0] == own[1][1] and own[0][1] > 7 and own[0][0] <= 7
 
 
-def test_shard_bounds_and_row_blocks_partition():
+def test_shard_bounds_and_owned_rows_partition():
     import sys
     sys.path.insert(0, ROOT)
     from paper_1809_09175_gb300 import shard as S
@@ -153,6 +172,18 @@ def test_shard_bounds_and_row_blocks_partition():
         assert b[0][0] == 0 and b[-1][1] == P_
         assert all(b[r][1] == b[r + 1][0] for r in range(G - 1))
         assert max(e - s for s, e in b) - min(e - s for s, e in b) <= 1
-    for I, G in [(1, 4), (7, 2), (1000, 8), (3, 5)]:
-        Bk = S.row_block(I, G)
-        assert Bk * G >= I and (Bk - 1) * G < I
+    # last rows per rank (-1: no nonzeros) -> owned [lo, hi): consecutive,
+    # covering [0, I), every last row owned by the first rank reaching it
+    cases = [([4, 9], 12), ([-1, 3, 3, 7], 8), ([5, 5, 5], 6), ([-1, -1, 0], 1), ([2, 2, -1], 10)]
+    for lasts, I in cases:
+        own = S.owned_rows(lasts, I)
+        assert own[0][0] == 0 and own[-1][1] == I
+        assert all(own[r][1] == own[r + 1][0] for r in range(len(own) - 1))
+        for r, L in enumerate(lasts):
+            if L >= 0:
+                first_reach = min(q for q in range(len(lasts)) if lasts[q] >= L)
+                assert S.row_owner(own, L) == first_reach
+    assert S.owned_rows([5, 5, 5], 6) == [(0, 6), (6, 6), (6, 6)]
+    assert S.owned_rows([-1, 3, 3, 7], 8) == [(0, 0), (0, 4), (4, 4), (4, 8)]
+    with pytest.raises(ValueError):
+        S.row_owner([(0, 2), (2, 2)], 2)
