@@ -251,9 +251,10 @@ class ShardedCPALS:
         return Grams
 
     def collective_bytes(self, factor_bytes: int) -> int:
-        """Bytes one iteration's collectives carry per rank (the sizes passed
-        to them; needs a completed step): the boundary-row buffers, the
-        broadcast factor rows, column norms, Grams and the two scalars."""
+        """Bytes of the buffers one iteration passes to its collectives: per
+        mode the shared-row buffer, the factor's rows (every rank's, through
+        the broadcasts), the column norms and the Gram; then the first
+        Grams and the fit's scalar (the one-time spans and ||X||^2 left out)."""
         acc = torch.tensor([], dtype=self.ops.acc_dtype).element_size()
         R, w, ld = self.R, self.world, self.ld
         per_mode = sum(w * ld * acc + I * ld * factor_bytes + R * 8 + R * R * 8 for I in self.dims)
