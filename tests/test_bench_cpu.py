@@ -55,3 +55,13 @@ def test_reference_arm_prints_the_contract_line():
         assert k in j, k
     assert j["impl"] == "reference" and j["value"] > 0
     assert j["cpu_baseline"]["kind"] == "oracle" and j["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_dram_traffic_record_matches_the_kernel_sources():
+    """The bench's roofline fraction divides the ncu-measured DRAM bytes of
+    the committed record by the kernel time; the record must have been taken
+    from the kernel sources as they are (their hash), else the bench reports
+    no traffic.  A change to the kernel sources needs a new capture."""
+    b = _bench().kernel_traffic(100_000_000)
+    assert b is not None
+    assert 16e8 <= b <= 40e8  # the 16-byte record stream plus factor-row misses, per 1e8 nonzeros
